@@ -1,0 +1,137 @@
+"""Pins of the oracle's decoders and ground-state search.
+
+  - the star and chain trees reproduce the paper's closed forms (App. A,
+    Eqs. 10-11) on arbitrary (leaked) physical states;
+  - every tree decoder is exact on constraint-satisfying states (App. A);
+  - Pruefer trees are spanning trees, and uniform over the N^(N-2) labelled
+    trees (Cayley) for N = 4;
+  - ME majority vote follows Eq. 4 with the hub breaking ties;
+  - the ground-state enumeration agrees with a brute force over all 2^N
+    states written independently here.
+"""
+import itertools
+from collections import Counter
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle as O
+import workloads as W
+
+
+def _random_phys(pb, rng):
+    s = np.where(rng.random(pb.n) < 0.5, -1, 1).astype(np.int8)
+    s[pb.used == 0] = 1
+    return s
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 8, 16])
+def test_star_and_chain_closed_forms(N):
+    pb = O.Problem("lhz", N, W.random_couplings(N, 2), 3)
+    rng = np.random.default_rng(N)
+    for _ in range(20):
+        q = _random_phys(pb, rng)
+        star = O.lhz_tree_decode(N, O.star_tree(N), q)
+        want_star = [1] + [int(q[O.lhz_index(N, 0, i)]) for i in range(1, N)]   # Eq. 11
+        assert star.tolist() == want_star
+        chain = O.lhz_tree_decode(N, O.chain_tree(N), q)
+        want_chain = [int(np.prod([q[O.lhz_index(N, m, m + 1)] for m in range(i)]))
+                      for i in range(N)]                                          # Eq. 10
+        assert chain.tolist() == want_chain
+
+
+@pytest.mark.parametrize("N", [3, 6, 9, 16])
+def test_tree_decoders_exact_without_leakage(N):
+    pb = O.Problem("lhz", N, W.random_couplings(N, 3), 3)
+    rng = np.random.default_rng(1)
+    trees = [O.star_tree(N), O.chain_tree(N)] + [O.prufer_tree(N, 5, 0, t) for t in range(7)]
+    for _ in range(25):
+        s = np.where(rng.random(N) < 0.5, -1, 1).astype(np.int8)
+        phys = pb.embed(s)
+        gauge = s * s[0]                                  # q_0 fixed to +1
+        for p in trees:
+            assert np.array_equal(O.lhz_tree_decode(N, p, phys), gauge)
+        assert np.array_equal(O.lhz_vote_decode(N, np.stack(trees[2:]), phys), gauge)
+
+
+@pytest.mark.parametrize("N", [2, 3, 7, 12])
+def test_prufer_gives_spanning_trees(N):
+    for t in range(20):
+        parent = O.prufer_tree(N, 77, 3, t)
+        assert parent[0] == -1
+        for v in range(1, N):
+            seen, x = set(), v
+            while x != 0:
+                assert x not in seen
+                seen.add(x)
+                x = int(parent[x])
+                assert 0 <= x < N
+
+
+def test_prufer_trees_uniform_n4():
+    """Cayley: 4^2 = 16 labelled trees on 4 vertices, drawn uniformly."""
+    N = 4
+    counts = Counter()
+    for inst in range(400):
+        for t in range(10):
+            p = O.prufer_tree(N, 123, inst, t)
+            edges = frozenset(frozenset((v, int(p[v]))) for v in range(1, N))
+            counts[edges] += 1
+    assert len(counts) == 16
+    assert stats.chisquare(list(counts.values())).pvalue > 1e-3
+
+
+def test_vote_over_trees_majority():
+    N = 5
+    pb = O.Problem("lhz", N, W.random_couplings(N, 9), 2)
+    rng = np.random.default_rng(4)
+    trees = np.stack([O.prufer_tree(N, 1, 0, t) for t in range(5)])
+    for _ in range(50):
+        q = _random_phys(pb, rng)
+        each = np.stack([O.lhz_tree_decode(N, p, q) for p in trees]).astype(int)
+        want = np.sign(each.sum(axis=0))                  # Eq. 5; 5 votes never tie
+        assert np.array_equal(O.lhz_vote_decode(N, trees, q), want)
+
+
+@pytest.mark.parametrize("N", [4, 8, 12, 16])
+def test_me_majority_vote(N):
+    pb = O.Problem("me", N, W.random_couplings(N, 4), 2)
+    rng = np.random.default_rng(N)
+    chains = pb.chain_sites.reshape(N, pb.Lc + 1)
+    for _ in range(50):
+        q = _random_phys(pb, rng)
+        out = O.me_decode(pb, q)
+        for i in range(N):
+            tot = int(q[chains[i]].astype(int).sum())
+            want = np.sign(tot) if tot != 0 else int(q[pb.hub[i]])
+            assert out[i] == want
+
+
+def _bruteforce_ground(N, J):
+    Jm = np.zeros((N, N))
+    Jm[np.triu_indices(N, 1)] = J
+    best = None
+    for s in itertools.product([1, -1], repeat=N):
+        s = np.array(s)
+        e = int(s @ Jm @ s)
+        best = e if best is None or e < best else best
+    return best
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 6, 8, 10])
+def test_ground_energy_bruteforce(N):
+    for seed in range(3):
+        J = W.random_couplings(N, 1000 * N + seed)
+        e, s = O.ground_energy(N, J)
+        assert e == _bruteforce_ground(N, J)
+        assert O.logical_energy(N, J, s) == e
+        assert O.logical_energy(N, J, -s) == e                # Z2 partner, h = 0
+
+
+def test_logical_energy_definition():
+    N = 5
+    J = W.random_couplings(N, 3)
+    s = np.array([1, -1, -1, 1, -1], np.int8)
+    e = sum(int(J[O.lhz_index(N, i, j)]) * s[i] * s[j] for i in range(N) for j in range(i + 1, N))
+    assert O.logical_energy(N, J, s) == e
