@@ -1,0 +1,351 @@
+"""Benchmark of the SQA hot path: spin-flip attempts/s on one GB300.
+
+Workload (one step): ME of K_8 on a 2x2 Chimera (24 used of 32 sites, chains
+of 3, J_F = -2 max|J|), 1024 instances x 256 replicas, L = 64 Trotter slices,
+1e4 sweeps of the linear schedule at beta = 10/max|J|.  A step runs the whole
+path on the device: initial spins, the 1e4 sweeps (one persistent launch),
+energies of every slice, the readout and its majority-vote decoding with
+success counts.  Inputs (couplings, tables) are resident when the timed region
+starts; L2 is flushed between steps by writing a 256 MiB buffer.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the CPU oracle (the only reference this method has:
+the paper publishes no code) on a bounded sample of the same workload.
+Under torchrun every rank runs the whole workload (weak scaling, independent
+replicas); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "spin-flip attempts/s batched vs one-launch-per-instance; p50/p99 job latency"
+UNIT = "attempts/s"
+# Integer operations one attempt needs in this formulation (per replica):
+# 16 random bits = 1/8 of a Philox4x32-10 block (10 rounds x 2 IMAD.WIDE +
+# 2 LOP3 = 40) -> 5; threshold-index extraction 2; table load, compare and
+# flip-mask update 3.  Work shared by the 32 replicas of a word is not counted.
+OPS_PER_ATTEMPT = 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps", type=int, default=10_000, help="sweeps per anneal (default: the workload's 1e4)")
+    ap.add_argument("--instances", type=int, default=1024)
+    ap.add_argument("--per-instance-sample", type=int, default=8,
+                    help="instances timed on the one-launch-per-instance path")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {}, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except FileNotFoundError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 8 for k in range(4)
+                          if r[4 + k].lower() == "active"})
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": reasons}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        return world, rank, local, dist
+    return 1, 0, 0, None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(cfg, seconds_budget=15.0, first_instance=0):
+    """The oracle, as it stands, on instance(s) of the workload: 32 replicas,
+    the first sweeps of the same 1e4-sweep schedule.  Returns (attempts/s,
+    description, attempts)."""
+    import oracle as O
+    N, L, pen, beta, S = cfg["N"], cfg["L"], cfg["penalty"], cfg["beta"], cfg["sweeps"]
+    A, B = O.linear_schedule(S)
+    pb = O.Problem("me", N, cfg["J"][first_instance], pen)
+    R = 32
+    q = O.SQA(pb, L, R, beta, A, B, cfg["seed"], first_instance)
+    n_used = int(pb.used.sum())
+    t0 = time.perf_counter()
+    t = 0
+    chunk = 50
+    while time.perf_counter() - t0 < seconds_budget and t + chunk <= S:
+        q.run(t, t + chunk)
+        t += chunk
+    dt = time.perf_counter() - t0
+    attempts = n_used * L * R * t
+    desc = f"instance {first_instance}, replicas 0-31, sweeps 0-{t - 1} of the {S}-sweep anneal, 1 thread"
+    return attempts / dt, desc, attempts
+
+
+def run_reference(args, cfg, world, rank, dist):
+    """Reference arm: the CPU oracle on a bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle as O
+    N, L, pen, beta, S = cfg["N"], cfg["L"], cfg["penalty"], cfg["beta"], cfg["sweeps"]
+    A, B = O.linear_schedule(S)
+    R, sweeps_per_step = 32, 300
+    times, total = [], 0
+    for k in range(args.warmup + args.steps):
+        inst = k % cfg["J"].shape[0]
+        pb = O.Problem("me", N, cfg["J"][inst], pen)
+        q = O.SQA(pb, L, R, beta, A, B, cfg["seed"], inst)
+        t0 = time.perf_counter()
+        q.run(0, sweeps_per_step)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            total += int(pb.used.sum()) * L * R * sweeps_per_step
+    value = total / sum(times)
+    sample = (f"per step: one instance of the workload, replicas 0-31, sweeps 0-{sweeps_per_step - 1} "
+              f"of the {S}-sweep anneal, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "instances": int(cfg["J"].shape[0]), "replicas": cfg["R"],
+                   "slices": L, "sweeps": S, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    world, rank, local, dist = dist_setup()
+    cfg = W.me_n8_batch_config(n_inst=args.instances, sweeps=args.sweeps)
+    if args.impl == "reference":
+        run_reference(args, cfg, world, rank, dist)
+        return
+
+    import torch
+    import oracle as O  # noqa: F401  (only the cpu_baseline leg calls it)
+    import paper_1603_03755_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    N, R, L, S, I = cfg["N"], cfg["R"], cfg["L"], cfg["sweeps"], cfg["J"].shape[0]
+    h = pkg.Handle(embedding="me", N=N, J=cfg["J"], penalty=cfg["penalty"], sweeps=S, R=R,
+                   seed=cfg["seed"], L=L, beta=cfg["beta"])
+    attempts = h.info["attempts_per_sweep"] * S
+    e_ground = pkg.ground_energy(N, cfg["J"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    E_dev = torch.empty((I, L, R), dtype=torch.int32, device=dev)
+    ro_dev = torch.empty((I, h.info["n_phys"], h.info["words"]), dtype=torch.uint32, device=dev)
+    log_dev = torch.empty((I, R, N), dtype=torch.int8, device=dev)
+    en_dev = torch.empty((I, R), dtype=torch.int64, device=dev)
+    succ_dev = torch.empty((I,), dtype=torch.int32, device=dev)
+    L_ = pkg.lib()
+    import ctypes as C
+
+    def device_step():
+        h.run(stream=sp)                                            # init + sweeps
+        L_.sqa_energies(h.handle, E_dev.data_ptr(), 1, sp)         # energies
+        L_.sqa_readout(h.handle, ro_dev.data_ptr(), 1, sp)         # readout
+        st = L_.sqa_decode(h.handle, 0, 0, log_dev.data_ptr(), en_dev.data_ptr(),
+                           C.c_void_p(e_ground.ctypes.data), succ_dev.data_ptr(), 1, sp)
+        assert st == 0
+
+    launches_per_step = h.info["launches_per_run"] + 3  # + energy, readout, decode kernels
+
+    # the dominant kernel's own duration, on the stream it runs on
+    def timed_sweeps():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            h.run(stream=sp)
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        device_step()
+    stream.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        stream.synchronize()
+        barrier(dist)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        device_step()
+        e1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        barrier(dist)
+        times.append(e0.elapsed_time(e1) / 1e3)
+    sweep_times = [timed_sweeps() for _ in range(2)]
+    clk = clocks.stop()
+    t_step = max_over_ranks(dist, statistics.mean(times))
+    value = world * attempts / t_step
+    # correctness of what was timed: success counts vs a host recount
+    succ = succ_dev.cpu().numpy()
+    en = en_dev.cpu().numpy()
+    assert np.array_equal(succ, (en == e_ground[:, None]).sum(axis=1))
+
+    # end to end through the public API with host buffers
+    e2e_times = []
+    for k in range(max(2, min(args.steps, 3))):
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh = pkg.Handle(embedding="me", N=N, J=cfg["J"], penalty=cfg["penalty"], sweeps=S, R=R,
+                        seed=cfg["seed"], L=L, beta=cfg["beta"])
+        hh.run(stream=sp)
+        logical, energy, succ_h = hh.decode("me_mv", 0, e_ground=e_ground, stream=sp)
+        dt = time.perf_counter() - t0
+        h2d = hh.info["h2d_bytes"]
+        hh.close()
+        e2e_times.append(max_over_ranks(dist, dt))
+    d2h = logical.nbytes + energy.nbytes + succ_h.nbytes
+    e2e_value = world * attempts / statistics.mean(e2e_times)
+
+    # the plain one-launch-per-instance path on a sample of instances
+    ns = max(1, min(args.per_instance_sample, I))
+    hp = pkg.Handle(embedding="me", N=N, J=cfg["J"][:ns], penalty=cfg["penalty"], sweeps=S, R=R,
+                    seed=cfg["seed"], L=L, beta=cfg["beta"])
+    hp.run_per_instance(stream=sp)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hp.run_per_instance(stream=sp)
+    e1.record(stream)
+    stream.synchronize()
+    per_inst_rate = hp.info["attempts_per_sweep"] * S / (e0.elapsed_time(e1) / 1e3)
+    same = np.array_equal(hp.state(stream=sp), h.state(stream=sp)[:ns])
+    hp.close()
+
+    if rank != 0:
+        barrier(dist)
+        return
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    f_mhz = (clk or {}).get("sm_mhz") or 1462.0
+    peaks, src = load_peaks()
+    peak_gops = n_sm * 4 * 32 * f_mhz * 1e6 / 1e9
+    t_sweep = statistics.mean(sweep_times)
+    achieved_gops = attempts * OPS_PER_ATTEMPT / t_sweep / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, desc, _ = cpu_oracle_sample(cfg)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": cfg["name"], "embedding": "me_chimera_2x2", "N": N, "instances": I,
+                   "replicas": R, "slices": L, "sweeps": S, "parallelism": "replicas",
+                   "l2": "flushed between steps (256 MiB write)"},
+        "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved_gops / peak_gops, "traffic": None,
+                     "kernel": "sweep_kernel", "ops_per_attempt": OPS_PER_ATTEMPT,
+                     "peak_basis": f"{n_sm} SMs x 4 SMSP x 32 lanes x {f_mhz:.0f} MHz (median SM clock under load)",
+                     "sweep_kernel_s": t_sweep},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "per_instance_path": {"value": per_inst_rate, "unit": UNIT, "instances_sampled": ns,
+                              "same_bits_as_batched": bool(same),
+                              "batched_over_per_instance": value / world / per_inst_rate},
+        "peaks_source": src,
+    }
+    print(json.dumps(out))
+    barrier(dist)
+
+
+if __name__ == "__main__":
+    main()

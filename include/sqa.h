@@ -1,0 +1,195 @@
+/*
+ * sqa.h -- C ABI of the GB300 (sm_103a) library for the simulated quantum
+ * annealing (SQA) and parallel tempering (PT) hot path of
+ *   T. Albash, W. Vinci, D. A. Lidar, "Simulated Quantum Annealing Comparison
+ *   between All-to-All Connectivity Schemes", arXiv:1603.03755.
+ *
+ * What the library computes
+ *   A fully connected logical Ising problem H_P = sum_{i<j} J_ij s_i s_j
+ *   (Eq. 1, h = 0 as in Sec. III) is embedded into a physical problem, either
+ *   by minor embedding on a Chimera graph (Sec. II A: chains of ceil(N/4)+1
+ *   spins coupled with -penalty) or by the LHZ scheme (Sec. II B, Eq. 2:
+ *   one spin per logical pair with local field J_ij and C(N-1,2) plaquette
+ *   constraints of strength penalty).  SQA runs single-spin Metropolis sweeps
+ *   over the L Trotter slices of the path-integral representation of
+ *   H(t) = A(t) H_X + B(t) H_P (Eq. 3, App. B); PT runs the same sweep at zero
+ *   transverse field on P temperature slots with neighbour swaps accepted with
+ *   probability min{1, exp[(E_{i+1}-E_i)(beta_{i+1}-beta_i)]} (Eq. 9).
+ *   Readouts are decoded by majority vote (Eqs. 4-5) or LHZ spanning trees
+ *   (App. A, Eqs. 10-11).
+ *
+ * Conventions
+ *   - Every call returns an sqa_status and never aborts the process.
+ *   - Spins are bits: bit 0 <-> sigma = +1, bit 1 <-> sigma = -1.  Replica r
+ *     of a (site, slice) lives in bit (r % 32) of word (r / 32).
+ *   - Physical sites use the canonical numbering of the embedding:
+ *     ME site ((r*Lc + c)*2 + u)*4 + k on an Lc x Lc Chimera (Lc = ceil(N/4),
+ *     u = 0 vertical shore, u = 1 horizontal shore); LHZ spin (i,j), i<j, at
+ *     i*N - i(i+1)/2 + (j-i-1).  Sites the embedding does not use read 0.
+ *   - Inputs are copied; output buffers belong to the caller.  "Device"
+ *     pointers are CUDA device addresses (e.g. from torch tensors); streams
+ *     are cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - A handle is used by one host thread at a time.
+ *   - Results are bit-reproducible: they depend only on the descriptor (J,
+ *     seed, ...) and never on batch composition, launch shape or device.
+ */
+#ifndef SQA_GB300_H
+#define SQA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SQA_OK = 0,
+    SQA_ERR_INVALID = -1,     /* bad argument; nothing was changed */
+    SQA_ERR_UNSUPPORTED = -2, /* valid but outside what this build supports */
+    SQA_ERR_NOMEM = -3,       /* device or host allocation failed */
+    SQA_ERR_CUDA = -4,        /* a CUDA call failed; see sqa_last_error() */
+    SQA_ERR_TIMEOUT = -5,     /* a bounded wait ran out */
+    SQA_ERR_NO_DEVICE = -6,   /* no CUDA device is visible */
+    SQA_ERR_BUSY = -7         /* resource in use (server full, job pending) */
+} sqa_status;
+
+typedef enum { SQA_EMB_ME_CHIMERA = 0, SQA_EMB_LHZ = 1 } sqa_embedding;
+typedef enum { SQA_KIND_SQA = 0, SQA_KIND_PT = 1 } sqa_kind;
+typedef enum {
+    SQA_DECODE_ME_MV = 0,     /* ME majority vote per chain (Eq. 4); ties -> hub spin */
+    SQA_DECODE_LHZ_TREES = 1, /* LHZ majority vote over n_trees random trees (Eq. 5) */
+    SQA_DECODE_LHZ_STAR = 2,  /* LHZ star tree q_i = q_{0,i} (Eq. 11) */
+    SQA_DECODE_LHZ_CHAIN = 3  /* LHZ chain tree q_i = prod_{m<i} q_{m,m+1} (Eq. 10) */
+} sqa_decode_method;
+
+/* Problem and program description.  All pointers are host pointers; the
+ * arrays are copied by sqa_create. */
+typedef struct {
+    int32_t kind;          /* sqa_kind */
+    int32_t embedding;     /* sqa_embedding */
+    int32_t n_logical;     /* N >= 2 (ME: N <= 64, LHZ: N <= 64) */
+    int32_t n_instances;   /* I >= 1 instances sharing every parameter but J */
+    const int32_t *J;      /* [I][N(N-1)/2], row-major upper triangle (i<j) */
+    const int32_t *h;      /* NULL, or [I][N] logical fields; non-zero -> UNSUPPORTED */
+    int32_t penalty;       /* > 0: ME chain coupling -penalty; LHZ constraint strength */
+    int32_t n_sweeps;      /* S >= 1 */
+    int32_t n_replicas;    /* R >= 1 independent chains per instance */
+    uint64_t seed;         /* keys every random stream */
+    /* SQA (kind == SQA_KIND_SQA) */
+    int32_t n_slices;      /* L, even, 2 <= L <= 1024 */
+    double beta;           /* > 0 */
+    const double *A;       /* [S] transverse-field schedule >= 0, or NULL for A = 1 - s */
+    const double *B;       /* [S] problem schedule >= 0, or NULL for B = s; s_t = (t+1/2)/S */
+    /* PT (kind == SQA_KIND_PT) */
+    int32_t n_temps;       /* P >= 1 */
+    const double *betas;   /* [P] strictly decreasing (coldest first), > 0 */
+    int32_t swap_every;    /* >= 1 sweeps between swap events */
+} sqa_desc;
+
+typedef struct sqa_handle sqa_handle;
+
+/* Sizes of a created handle. */
+typedef struct {
+    int32_t n_phys;        /* canonical physical sites (readout row length) */
+    int32_t n_used;        /* sites the embedding uses */
+    int32_t n_terms;       /* physical terms (couplers, fields, constraints) */
+    int32_t z;             /* L for SQA, P for PT */
+    int32_t words;         /* W = ceil(R / 32) */
+    int32_t delta_min, delta_max; /* range of single-flip energy changes */
+    int64_t attempts_per_sweep;   /* I * n_used * Z * R */
+    int64_t device_bytes;  /* device memory held by the handle */
+    int64_t h2d_bytes;     /* bytes sqa_create copied host -> device */
+    int32_t launches_per_run; /* kernel launches of one sqa_run */
+    int32_t pad_;
+} sqa_info;
+
+/* Builds the embedding (Sec. II A/B), the acceptance tables (uint32
+ * thresholds floor(2^32 e^-x), computed on the host in double) and the
+ * device state; draws the initial spins.  Synchronous.  On error *out is
+ * NULL. */
+sqa_status sqa_create(const sqa_desc *desc, sqa_handle **out);
+void sqa_destroy(sqa_handle *h);
+sqa_status sqa_get_info(const sqa_handle *h, sqa_info *out);
+
+/* Runs the whole program: fresh initial spins, then sweeps 0..S-1 (SQA
+ * anneal, or PT with swaps every swap_every sweeps), as one persistent
+ * launch over all instances.  Asynchronous on stream. */
+sqa_status sqa_run(sqa_handle *h, void *stream);
+
+/* Sweeps t0..t1-1 continuing from the current state (t0 == 0 draws fresh
+ * initial spins first).  Runs split at any t give the same bits as one run
+ * (checkpoint/resume). */
+sqa_status sqa_run_sweeps(sqa_handle *h, int32_t t0, int32_t t1, void *stream);
+
+/* The plain path kept for comparison: the same sweeps as sqa_run, but one
+ * kernel launch per instance, in sequence on stream.  Same bits. */
+sqa_status sqa_run_per_instance(sqa_handle *h, void *stream);
+
+/* Parallel tempering on the handle's problem (App. B): switches the handle to
+ * PT with the given ladder (betas strictly decreasing, coldest first), draws
+ * fresh spins and runs n_sweeps sweeps with swaps every swap_every sweeps. */
+sqa_status pt_run(sqa_handle *h, const double *betas, int32_t n_temps, int32_t n_sweeps,
+                  int32_t swap_every, void *stream);
+
+/* One persistent launch over the units of several handles of any shapes
+ * (ragged batching); each handle runs its whole program as in sqa_run. */
+sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream);
+
+/* Readout: slice 0 (SQA) or the coldest slot (PT); out [I][n_phys][W]. */
+sqa_status sqa_readout(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *stream);
+/* Whole state; out [I][Z][n_phys][W]. */
+sqa_status sqa_state(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *stream);
+/* Physical energy E_P of every slice/slot and replica; out [I][Z][R]. */
+sqa_status sqa_energies(sqa_handle *h, int32_t *out, int32_t out_is_device, void *stream);
+
+/* Decodes the readout of every replica to a logical state and its logical
+ * energy (Eq. 1).  method: sqa_decode_method (ME handles take ME_MV, LHZ
+ * handles the LHZ methods).  n_trees: votes for LHZ_TREES (odd; 0 ->
+ * ceil(N/4)+1 made odd).  logical_out [I][R][N] int8 (+-1; LHZ fixes
+ * logical spin 0 to +1), energy_out [I][R].  If e_ground (host, [I]) is not
+ * NULL, success_out [I] counts replicas whose decoded energy equals it.
+ * Any output may be NULL. */
+sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *logical_out,
+                      int64_t *energy_out, const int64_t *e_ground, int32_t *success_out,
+                      int32_t out_is_device, void *stream);
+
+/* Exact logical ground-state energies by exhaustive search over the 2^(N-1)
+ * states with s_{N-1} = +1 (h = 0), on the GPU.  J host [I][N(N-1)/2];
+ * e_out host [I].  N <= 40.  Synchronous. */
+sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, int64_t *e_out);
+
+/* ---- host-only views of the library's planning (no device needed) ---- */
+
+/* The physical problem the library builds for one instance (Sec. II A/B):
+ * terms w * prod(sigma) in canonical site numbering.  term_mem is
+ * [cap_terms][4] (-1 pads), colour [n_phys] (-1 for unused sites).  J is
+ * [N(N-1)/2].  Fails with SQA_ERR_INVALID if cap_terms is too small. */
+sqa_status sqa_plan_terms(int32_t embedding, int32_t N, const int32_t *J, int32_t penalty,
+                          int32_t cap_terms, int32_t *n_phys, int32_t *n_terms,
+                          int32_t *term_size, int32_t *term_mem, int32_t *term_w,
+                          int32_t *colour);
+
+/* The acceptance thresholds sqa_create would upload for desc: SQA
+ * [S][nd][3] indexed by ((delta - dmin)/2, (m + 2)/2), PT [P][nd] indexed
+ * by (delta - dmin)/2, nd = (dmax - dmin)/2 + 1.  cap is the length of T. */
+sqa_status sqa_plan_tables(const sqa_desc *desc, uint32_t *T, int64_t cap, int32_t *dmin,
+                           int32_t *dmax);
+
+/* PT swap thresholds of slots (pair, pair+1) (Eq. 9): out[dE-1] for
+ * dE = 1..*len, zero beyond. */
+sqa_status sqa_plan_swap_table(const double *betas, int32_t n_temps, int32_t pair, uint32_t *out,
+                               int32_t cap, int32_t *len);
+
+/* The random spanning tree number `tree` of instance `inst` used by
+ * SQA_DECODE_LHZ_TREES: parent[v], parent[0] = -1. */
+sqa_status sqa_plan_tree(int32_t N, uint64_t seed, int32_t inst, int32_t tree, int32_t *parent);
+
+const char *sqa_strerror(sqa_status s);
+/* Detail of the last error on this thread (CUDA message, bad field). */
+const char *sqa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

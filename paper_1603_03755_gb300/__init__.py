@@ -1,0 +1,248 @@
+"""GB300 (sm_103a) library for the SQA / PT hot path of arXiv:1603.03755.
+
+A thin ctypes binding over ``_build/libsqa_gb300.so`` (C ABI in
+``include/sqa.h``).  Every step of the path runs in the library's CUDA
+kernels; this module only marshals arguments.  PyTorch supplies device
+buffers and streams.  There is no CPU fallback: importing works without a
+GPU, but every compute call needs the compiled library and a CUDA device and
+raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SQA_OK, SQA_ERR_INVALID, SQA_ERR_UNSUPPORTED, SQA_ERR_NOMEM = 0, -1, -2, -3
+SQA_ERR_CUDA, SQA_ERR_TIMEOUT, SQA_ERR_NO_DEVICE, SQA_ERR_BUSY = -4, -5, -6, -7
+EMB = {"me": 0, "lhz": 1}
+KIND = {"sqa": 0, "pt": 1}
+DECODE = {"me_mv": 0, "lhz_trees": 1, "lhz_star": 2, "lhz_chain": 3}
+
+LIB_PATH = _build.LIB
+
+
+class SQAError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({detail})")
+
+
+class _Desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("embedding", C.c_int32), ("n_logical", C.c_int32),
+                ("n_instances", C.c_int32), ("J", C.c_void_p), ("h", C.c_void_p),
+                ("penalty", C.c_int32), ("n_sweeps", C.c_int32), ("n_replicas", C.c_int32),
+                ("seed", C.c_uint64), ("n_slices", C.c_int32), ("beta", C.c_double),
+                ("A", C.c_void_p), ("B", C.c_void_p), ("n_temps", C.c_int32),
+                ("betas", C.c_void_p), ("swap_every", C.c_int32)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("n_phys", C.c_int32), ("n_used", C.c_int32), ("n_terms", C.c_int32),
+                ("z", C.c_int32), ("words", C.c_int32), ("delta_min", C.c_int32),
+                ("delta_max", C.c_int32), ("attempts_per_sweep", C.c_int64),
+                ("device_bytes", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("launches_per_run", C.c_int32), ("pad_", C.c_int32)]
+
+
+# Every symbol the header declares, with its ctypes signature.
+_SIGS = {
+    "sqa_create": (C.c_int, [C.POINTER(_Desc), C.POINTER(C.c_void_p)]),
+    "sqa_destroy": (None, [C.c_void_p]),
+    "sqa_get_info": (C.c_int, [C.c_void_p, C.POINTER(_Info)]),
+    "sqa_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sqa_run_sweeps": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    "sqa_run_per_instance": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "pt_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    "sqa_batch_run": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_readout": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_energies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_decode": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_ground_energy": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "sqa_plan_terms": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sqa_plan_tables": (C.c_int, [C.POINTER(_Desc), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
+    "sqa_plan_swap_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_plan_tree": (C.c_int, [C.c_int32, C.c_uint64, C.c_int32, C.c_int32, C.c_void_p]),
+    "sqa_strerror": (C.c_char_p, [C.c_int]),
+    "sqa_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded library.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1603_03755_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != SQA_OK:
+        detail = lib().sqa_last_error().decode(errors="replace")
+        raise SQAError(status, where, detail)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x):
+    """(address, is_device) of a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data, 0
+    assert x.is_contiguous()
+    return x.data_ptr(), int(x.is_cuda)
+
+
+class Handle:
+    """One problem (I instances sharing every parameter but J) and its
+    resident device state.  ``kind`` 'sqa' or 'pt'; ``embedding`` 'me' or
+    'lhz'.  J has shape [I, N(N-1)/2] (int32)."""
+
+    def __init__(self, *, embedding: str, N: int, J, penalty: int, sweeps: int, R: int,
+                 seed: int = 0, kind: str = "sqa", L: int = 32, beta: float = 1.0, A=None, B=None,
+                 betas=None, swap_every: int = 1):
+        J = np.ascontiguousarray(np.atleast_2d(np.asarray(J, np.int32)))
+        self.N, self.I, self.R, self.kind, self.embedding = N, J.shape[0], R, kind, embedding
+        self._keep = [J]
+        d = _Desc()
+        d.kind, d.embedding, d.n_logical, d.n_instances = KIND[kind], EMB[embedding], N, self.I
+        d.J = J.ctypes.data
+        d.h = None
+        d.penalty, d.n_sweeps, d.n_replicas, d.seed = int(penalty), int(sweeps), int(R), int(seed)
+        d.n_slices, d.beta = int(L), float(beta)
+        if A is not None:
+            A = np.ascontiguousarray(A, np.float64)
+            B = np.ascontiguousarray(B, np.float64)
+            self._keep += [A, B]
+            d.A, d.B = A.ctypes.data, B.ctypes.data
+        if betas is not None:
+            betas = np.ascontiguousarray(betas, np.float64)
+            self._keep.append(betas)
+            d.betas, d.n_temps = betas.ctypes.data, len(betas)
+        d.swap_every = int(swap_every)
+        h = C.c_void_p()
+        _check(lib().sqa_create(C.byref(d), C.byref(h)), "sqa_create")
+        self._h = h
+        self._refresh_info()
+
+    def _refresh_info(self):
+        info = _Info()
+        _check(lib().sqa_get_info(self._h, C.byref(info)), "sqa_get_info")
+        self.info = {k: getattr(info, k) for k, _ in _Info._fields_}
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sqa_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    # ---- running ----
+    def run(self, stream=None):
+        _check(lib().sqa_run(self._h, _stream_ptr(stream)), "sqa_run")
+
+    def run_sweeps(self, t0: int, t1: int, stream=None):
+        _check(lib().sqa_run_sweeps(self._h, t0, t1, _stream_ptr(stream)), "sqa_run_sweeps")
+
+    def run_per_instance(self, stream=None):
+        _check(lib().sqa_run_per_instance(self._h, _stream_ptr(stream)), "sqa_run_per_instance")
+
+    def pt_run(self, betas, sweeps: int, swap_every: int, stream=None):
+        b = np.ascontiguousarray(betas, np.float64)
+        _check(lib().pt_run(self._h, b.ctypes.data, len(b), sweeps, swap_every, _stream_ptr(stream)), "pt_run")
+        self.kind = "pt"
+        self._refresh_info()
+
+    # ---- outputs (numpy on the host, or torch tensors given as out=) ----
+    def _words_out(self, fn, zc, out, stream):
+        shape = (self.I, zc, self.info["n_phys"], self.info["words"])
+        if out is None:
+            out = np.zeros(shape, np.uint32)
+        p, dev = _ptr(out)
+        _check(fn(self._h, p, dev, _stream_ptr(stream)), fn.__name__)
+        return out
+
+    def readout(self, out=None, stream=None):
+        """Slice 0 / coldest slot, [I, n_phys, W] uint32."""
+        if out is None:
+            out = np.zeros((self.I, self.info["n_phys"], self.info["words"]), np.uint32)
+        p, dev = _ptr(out)
+        _check(lib().sqa_readout(self._h, p, dev, _stream_ptr(stream)), "sqa_readout")
+        return out
+
+    def state(self, out=None, stream=None):
+        """All slices / slots, [I, Z, n_phys, W] uint32."""
+        return self._words_out(lib().sqa_state, self.info["z"], out, stream)
+
+    def energies(self, out=None, stream=None):
+        """E_P per (instance, slice/slot, replica), [I, Z, R] int32."""
+        if out is None:
+            out = np.zeros((self.I, self.info["z"], self.R), np.int32)
+        p, dev = _ptr(out)
+        _check(lib().sqa_energies(self._h, p, dev, _stream_ptr(stream)), "sqa_energies")
+        return out
+
+    def decode(self, method: str | None = None, n_trees: int = 0, e_ground=None, stream=None):
+        """Host arrays: logical [I, R, N] int8, energy [I, R] int64, success [I] int32
+        (None unless e_ground is given)."""
+        if method is None:
+            method = "me_mv" if self.embedding == "me" else "lhz_trees"
+        logical = np.zeros((self.I, self.R, self.N), np.int8)
+        energy = np.zeros((self.I, self.R), np.int64)
+        succ = np.zeros(self.I, np.int32)
+        eg = None
+        if e_ground is not None:
+            eg = np.ascontiguousarray(e_ground, np.int64)
+        _check(lib().sqa_decode(self._h, DECODE[method], n_trees, logical.ctypes.data,
+                                energy.ctypes.data, None if eg is None else eg.ctypes.data,
+                                succ.ctypes.data if eg is not None else None, 0, _stream_ptr(stream)),
+               "sqa_decode")
+        return logical, energy, (succ if eg is not None else None)
+
+
+def batch_run(handles, stream=None):
+    """One persistent launch over every unit of several handles."""
+    arr = (C.c_void_p * len(handles))(*[h.handle for h in handles])
+    _check(lib().sqa_batch_run(arr, len(handles), _stream_ptr(stream)), "sqa_batch_run")
+
+
+def ground_energy(N: int, J) -> np.ndarray:
+    """Exact logical ground-state energies on the GPU, J [I, N(N-1)/2]."""
+    J = np.ascontiguousarray(np.atleast_2d(np.asarray(J, np.int32)))
+    out = np.zeros(J.shape[0], np.int64)
+    _check(lib().sqa_ground_energy(N, J.shape[0], J.ctypes.data, out.ctypes.data), "sqa_ground_energy")
+    return out
+
+
+def unpack_words(words, R: int) -> np.ndarray:
+    """[..., W] uint32 -> [..., R] int8 sigma (+1 / -1)."""
+    w = np.asarray(words, np.uint32)
+    bits = (w[..., None] >> np.arange(32, dtype=np.uint32)) & 1
+    bits = bits.reshape(w.shape[:-1] + (w.shape[-1] * 32,))[..., :R]
+    return np.where(bits == 1, -1, 1).astype(np.int8)

@@ -1,0 +1,795 @@
+// C ABI of the SQA / PT library (include/sqa.h): handle lifecycle, launch
+// planning and the host side of every entry point.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "philox.cuh"
+#include "sqa_internal.h"
+
+namespace sqa {
+
+__global__ void init_kernel(JobDev J, const int *canon);
+__global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units, int *counter);
+__global__ void energy_kernel(JobDev J, int32_t *out);
+__global__ void canon_kernel(JobDev J, const int *compact_of, int z0, int zcount, uint32_t *out);
+__global__ void decode_kernel(JobDev J, DecodeArgs D);
+__global__ void ground_kernel(int N, const int32_t *J, int chunk_bits, int64_t n_chunks,
+                              unsigned long long *best);
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+static sqa_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return SQA_ERR_CUDA;
+}
+
+#define SQA_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr int kThreads = 256;
+constexpr int kSmemLimit = 227 * 1024;
+
+static int g_num_sms = 0;
+
+static sqa_status device_ready()
+{
+    int dev = 0, n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        g_err = "no CUDA device";
+        return SQA_ERR_NO_DEVICE;
+    }
+    SQA_CUDA(cudaGetDevice(&dev));
+    if (g_num_sms == 0) {
+        cudaDeviceProp prop;
+        SQA_CUDA(cudaGetDeviceProperties(&prop, dev));
+        g_num_sms = prop.multiProcessorCount;
+        SQA_CUDA(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+    }
+    return SQA_OK;
+}
+
+}  // namespace sqa
+
+using namespace sqa;
+
+struct sqa_handle {
+    // copied description
+    int kind = 0, emb = 0, N = 0, I = 0, penalty = 0, S = 0, R = 0, L = 0, P = 0, swap_every = 1;
+    uint64_t seed = 0;
+    double beta = 0;
+    std::vector<int32_t> J;
+    std::vector<double> A, B, betas;
+    Plan plan;
+    int smax = 0, dmin = 0, dmax = 0, nd = 0;
+    // device
+    JobDev job{};
+    uint32_t *d_state = nullptr;
+    SiteRec *d_sites = nullptr;
+    uint32_t *d_T = nullptr;
+    ETerm *d_eterms = nullptr;
+    uint32_t *d_Tsw = nullptr;
+    int *d_swoff = nullptr, *d_swlen = nullptr;
+    int *d_canon = nullptr, *d_compact = nullptr;
+    int32_t *d_J = nullptr;
+    int *d_chain = nullptr, *d_pair = nullptr;
+    int *d_parents = nullptr, *d_orders = nullptr;
+    int cur_trees = -1, cur_tree_kind = -1;
+    JobDev *d_job = nullptr;
+    Unit *d_units = nullptr;
+    int n_units = 0;
+    int *d_counter = nullptr;
+    std::vector<Unit> units;
+    int64_t device_bytes = 0;
+    int64_t h2d_bytes = 0;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+template <typename T>
+sqa_status dalloc(sqa_handle *h, T **p, size_t count)
+{
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return SQA_ERR_NOMEM;
+    }
+    h->allocs.push_back(q);
+    h->device_bytes += (int64_t)bytes;
+    *p = (T *)q;
+    return SQA_OK;
+}
+
+template <typename T>
+sqa_status upload(sqa_handle *h, T **p, const std::vector<T> &v)
+{
+    sqa_status st = dalloc(h, p, v.size());
+    if (st != SQA_OK) return st;
+    if (!v.empty()) SQA_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    h->h2d_bytes += (int64_t)(v.size() * sizeof(T));
+    return SQA_OK;
+}
+
+void free_all(sqa_handle *h)
+{
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+    h->device_bytes = 0;
+    h->h2d_bytes = 0;
+}
+
+// Shared memory of one unit of wc words.
+int unit_smem(const JobDev &J, int wc, int *zstride_out)
+{
+    int zs = J.n * wc;
+    // items of consecutive lanes differ by one word, then by one z step
+    // (SQA steps two slices); pad the row so lanes fall on distinct banks
+    if (J.kind == SQA_KIND_SQA) {
+        if (wc % 2 == 0) {
+            while ((2 * zs) % 32 != wc % 32) zs++;
+        } else {
+            while (zs % 2 == 0) zs++;
+        }
+    } else {
+        while (zs % 32 != wc % 32) zs++;
+    }
+    *zstride_out = zs;
+    size_t off = (size_t)J.Z * zs * 4;
+    off += (size_t)(J.kind == SQA_KIND_SQA ? J.nrow : J.Z * J.nrow) * 4;
+    off = (off + 15) & ~(size_t)15;
+    off += (size_t)J.n * sizeof(SiteRec);
+    if (J.kind == SQA_KIND_PT) {
+        off += (size_t)J.Z * wc * 32 * 4;
+        off += (size_t)(J.Z / 2 + 1) * wc * 4;
+    }
+    return (int)off;
+}
+
+// Choose the words per unit: as many as fit a shared-memory budget that
+// leaves room for two resident blocks.
+void plan_units(sqa_handle *h)
+{
+    JobDev &J = h->job;
+    const int budget = kSmemLimit / 2 - 1024;
+    int wc = J.W, zs = 0;
+    while (wc > 1 && unit_smem(J, wc, &zs) > budget) wc = (wc + 1) / 2;
+    J.smem_bytes = unit_smem(J, wc, &zs);
+    J.zstride = zs;
+    J.wc = wc;
+    h->units.clear();
+    for (int i = 0; i < h->I; i++)
+        for (int w0 = 0; w0 < J.W; w0 += wc) h->units.push_back(Unit{0, i, w0, std::min(wc, J.W - w0)});
+}
+
+sqa_status validate(const sqa_desc *d)
+{
+    if (!d) return set_error("desc is NULL"), SQA_ERR_INVALID;
+    if (d->kind != SQA_KIND_SQA && d->kind != SQA_KIND_PT) return set_error("kind"), SQA_ERR_INVALID;
+    if (d->embedding != SQA_EMB_ME_CHIMERA && d->embedding != SQA_EMB_LHZ)
+        return set_error("embedding"), SQA_ERR_INVALID;
+    if (d->n_logical < 2 || d->n_logical > kMaxN) return set_error("n_logical out of range"), SQA_ERR_INVALID;
+    if (d->n_instances < 1 || !d->J) return set_error("n_instances / J"), SQA_ERR_INVALID;
+    if (d->penalty <= 0) return set_error("penalty must be > 0"), SQA_ERR_INVALID;
+    if (d->n_sweeps < 1 || d->n_replicas < 1) return set_error("n_sweeps / n_replicas"), SQA_ERR_INVALID;
+    if (d->h) {
+        for (int64_t i = 0; i < (int64_t)d->n_instances * d->n_logical; i++)
+            if (d->h[i] != 0) return set_error("non-zero logical fields need an ancilla"), SQA_ERR_UNSUPPORTED;
+    }
+    if (d->kind == SQA_KIND_SQA) {
+        if (d->n_slices < 2 || (d->n_slices & 1) || d->n_slices > 1024)
+            return set_error("n_slices must be even, 2..1024"), SQA_ERR_INVALID;
+        if (!(d->beta > 0) || !isfinite(d->beta)) return set_error("beta"), SQA_ERR_INVALID;
+        if ((d->A == nullptr) != (d->B == nullptr)) return set_error("give both A and B or neither"), SQA_ERR_INVALID;
+        if (d->A)
+            for (int t = 0; t < d->n_sweeps; t++)
+                if (!(d->A[t] >= 0) || !(d->B[t] >= 0) || !isfinite(d->A[t]) || !isfinite(d->B[t]))
+                    return set_error("schedule values must be finite and >= 0"), SQA_ERR_INVALID;
+    } else {
+        if (d->n_temps < 1 || !d->betas || d->swap_every < 1) return set_error("PT ladder"), SQA_ERR_INVALID;
+        for (int p = 0; p < d->n_temps; p++)
+            if (!(d->betas[p] > 0) || !isfinite(d->betas[p])) return set_error("betas must be > 0"), SQA_ERR_INVALID;
+        for (int p = 0; p + 1 < d->n_temps; p++)
+            if (!(d->betas[p] > d->betas[p + 1])) return set_error("betas must decrease"), SQA_ERR_INVALID;
+    }
+    return SQA_OK;
+}
+
+// (Re)build the program-dependent part: tables, site records, state.
+sqa_status setup_program(sqa_handle *h)
+{
+    free_all(h);
+    const Plan &pl = h->plan;
+    const int N = h->N, npair = N * (N - 1) / 2;
+    h->smax = 0;
+    for (int i = 0; i < h->I; i++)
+        h->smax = std::max(h->smax, site_weight_sum_max(pl, h->J.data() + (size_t)i * npair, h->penalty));
+    const int K = h->kind == SQA_KIND_SQA ? 6 : 2;
+    if (K * h->smax + 2 > kMaxByteWindow) {
+        set_error("penalty/couplings too large for the byte-wise threshold window");
+        return SQA_ERR_UNSUPPORTED;
+    }
+    h->dmin = -2 * h->smax;
+    h->dmax = 2 * h->smax;
+    h->nd = (h->dmax - h->dmin) / 2 + 1;
+    JobDev &J = h->job;
+    J = JobDev{};
+    J.kind = h->kind;
+    J.n = pl.n;
+    J.n_phys = pl.n_phys;
+    J.Z = h->kind == SQA_KIND_SQA ? h->L : h->P;
+    J.W = (h->R + 31) / 32;
+    J.R = h->R;
+    J.n_inst = h->I;
+    J.ncol = pl.ncol;
+    for (int c = 0; c <= kMaxColours; c++) J.col_ptr[c] = pl.col_ptr[c];
+    J.nrow = h->kind == SQA_KIND_SQA ? 3 * h->nd : h->nd;
+    J.n_eterms = (int)pl.terms.size();
+    J.swap_every = h->swap_every;
+    J.t0 = 0;
+    J.t1 = h->S;
+    J.seed_lo = (uint32_t)h->seed;
+    const uint32_t shi = (uint32_t)(h->seed >> 32);
+    J.key_hi = shi ^ kDomSweepHi;
+    J.key_lo = shi ^ kDomSweepLo;
+    J.key_swap = shi ^ kDomSwap;
+
+    std::vector<SiteRec> sites, all_sites;
+    std::vector<ETerm> et, all_et;
+    for (int i = 0; i < h->I; i++) {
+        const int32_t *Ji = h->J.data() + (size_t)i * npair;
+        build_sites(pl, Ji, h->penalty, K, h->smax, sites);
+        all_sites.insert(all_sites.end(), sites.begin(), sites.end());
+        build_eterms(pl, Ji, h->penalty, et);
+        all_et.insert(all_et.end(), et.begin(), et.end());
+    }
+    std::vector<uint32_t> T, Tsw;
+    std::vector<int> swoff, swlen;
+    if (h->kind == SQA_KIND_SQA) {
+        sqa_tables(h->A.data(), h->B.data(), h->beta, h->L, h->S, h->dmin, h->dmax, T);
+    } else {
+        pt_tables(h->betas.data(), h->P, h->dmin, h->dmax, T);
+        swap_tables(h->betas.data(), h->P, Tsw, swoff, swlen);
+    }
+    sqa_status st;
+    if ((st = dalloc(h, &h->d_state, (size_t)h->I * J.Z * J.n * J.W)) != SQA_OK) return st;
+    if ((st = upload(h, &h->d_sites, all_sites)) != SQA_OK) return st;
+    if ((st = upload(h, &h->d_eterms, all_et)) != SQA_OK) return st;
+    if ((st = upload(h, &h->d_T, T)) != SQA_OK) return st;
+    if (h->kind == SQA_KIND_PT) {
+        if ((st = upload(h, &h->d_Tsw, Tsw)) != SQA_OK) return st;
+        if ((st = upload(h, &h->d_swoff, swoff)) != SQA_OK) return st;
+        if ((st = upload(h, &h->d_swlen, swlen)) != SQA_OK) return st;
+    }
+    if ((st = upload(h, &h->d_canon, pl.canon)) != SQA_OK) return st;
+    if ((st = upload(h, &h->d_compact, pl.compact)) != SQA_OK) return st;
+    if ((st = upload(h, &h->d_J, h->J)) != SQA_OK) return st;
+    if (h->emb == SQA_EMB_ME_CHIMERA) {
+        if ((st = upload(h, &h->d_chain, pl.chain)) != SQA_OK) return st;
+    } else {
+        if ((st = upload(h, &h->d_pair, pl.pair)) != SQA_OK) return st;
+    }
+    h->cur_trees = -1;
+    J.state = h->d_state;
+    J.sites = h->d_sites;
+    J.T = h->d_T;
+    J.eterms = h->d_eterms;
+    J.Tsw = h->d_Tsw;
+    J.sw_off = h->d_swoff;
+    J.sw_len = h->d_swlen;
+    plan_units(h);
+    if ((st = dalloc(h, &h->d_job, 1)) != SQA_OK) return st;
+    if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) return st;
+    h->n_units = (int)h->units.size();
+    if ((st = dalloc(h, &h->d_counter, 1)) != SQA_OK) return st;
+    return SQA_OK;
+}
+
+sqa_status launch_init(sqa_handle *h, cudaStream_t s)
+{
+    const int64_t total = (int64_t)h->I * h->job.Z * h->job.n * h->job.W;
+    const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 4 * 1024);
+    init_kernel<<<std::max(blocks, 1), kThreads, 0, s>>>(h->job, h->d_canon);
+    SQA_CUDA(cudaGetLastError());
+    return SQA_OK;
+}
+
+int grid_for(int smem_bytes, int n_units)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, kThreads, smem_bytes);
+    per_sm = std::max(per_sm, 1);
+    return std::max(1, std::min(n_units, per_sm * g_num_sms));
+}
+
+// One launch of the sweep kernel over units [u0, u0+nu) of one handle.
+sqa_status launch_sweeps(sqa_handle *h, int t0, int t1, int u0, int nu, cudaStream_t s)
+{
+    h->job.t0 = t0;
+    h->job.t1 = t1;
+    SQA_CUDA(cudaMemcpyAsync(h->d_job, &h->job, sizeof(JobDev), cudaMemcpyHostToDevice, s));
+    SQA_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
+    const int grid = grid_for(h->job.smem_bytes, nu);
+    sweep_kernel<<<grid, kThreads, h->job.smem_bytes, s>>>(h->d_job, h->d_units + u0, nu, h->d_counter);
+    SQA_CUDA(cudaGetLastError());
+    return SQA_OK;
+}
+
+sqa_status decode_trees(sqa_handle *h, int method, int n_trees)
+{
+    if (h->cur_trees == n_trees && h->cur_tree_kind == method) return SQA_OK;
+    const int N = h->N;
+    std::vector<int> par((size_t)h->I * n_trees * N), ord((size_t)h->I * n_trees * N);
+    for (int i = 0; i < h->I; i++)
+        for (int t = 0; t < n_trees; t++) {
+            int *p = par.data() + ((size_t)i * n_trees + t) * N;
+            int *o = ord.data() + ((size_t)i * n_trees + t) * N;
+            if (method == SQA_DECODE_LHZ_TREES)
+                prufer_tree(N, h->seed, i, t, p, o);
+            else if (method == SQA_DECODE_LHZ_STAR)
+                star_tree(N, p, o);
+            else
+                chain_tree(N, p, o);
+        }
+    sqa_status st;
+    if ((st = upload(h, &h->d_parents, par)) != SQA_OK) return st;
+    if ((st = upload(h, &h->d_orders, ord)) != SQA_OK) return st;
+    h->cur_trees = n_trees;
+    h->cur_tree_kind = method;
+    return SQA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sqa_strerror(sqa_status s)
+{
+    switch (s) {
+    case SQA_OK: return "ok";
+    case SQA_ERR_INVALID: return "invalid argument";
+    case SQA_ERR_UNSUPPORTED: return "unsupported";
+    case SQA_ERR_NOMEM: return "out of memory";
+    case SQA_ERR_CUDA: return "CUDA error";
+    case SQA_ERR_TIMEOUT: return "timeout";
+    case SQA_ERR_NO_DEVICE: return "no CUDA device";
+    case SQA_ERR_BUSY: return "busy";
+    }
+    return "unknown status";
+}
+
+const char *sqa_last_error(void) { return g_err.c_str(); }
+
+sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
+{
+    if (!out) return set_error("out is NULL"), SQA_ERR_INVALID;
+    *out = nullptr;
+    sqa_status st = validate(d);
+    if (st != SQA_OK) return st;
+    if ((st = device_ready()) != SQA_OK) return st;
+    sqa_handle *h = new (std::nothrow) sqa_handle();
+    if (!h) return SQA_ERR_NOMEM;
+    h->kind = d->kind;
+    h->emb = d->embedding;
+    h->N = d->n_logical;
+    h->I = d->n_instances;
+    h->penalty = d->penalty;
+    h->S = d->n_sweeps;
+    h->R = d->n_replicas;
+    h->seed = d->seed;
+    const int npair = h->N * (h->N - 1) / 2;
+    h->J.assign(d->J, d->J + (size_t)h->I * npair);
+    if (d->kind == SQA_KIND_SQA) {
+        h->L = d->n_slices;
+        h->beta = d->beta;
+        h->A.resize(h->S);
+        h->B.resize(h->S);
+        for (int t = 0; t < h->S; t++) {
+            if (d->A) {
+                h->A[t] = d->A[t];
+                h->B[t] = d->B[t];
+            } else {
+                const double s = ((double)t + 0.5) / (double)h->S;
+                h->A[t] = 1.0 - s;
+                h->B[t] = s;
+            }
+        }
+    } else {
+        h->P = d->n_temps;
+        h->betas.assign(d->betas, d->betas + h->P);
+        h->swap_every = d->swap_every;
+    }
+    std::string err;
+    if (!build_plan(h->emb, h->N, h->plan, err)) {
+        delete h;
+        return set_error(err), SQA_ERR_UNSUPPORTED;
+    }
+    st = setup_program(h);
+    if (st == SQA_OK) st = launch_init(h, 0);
+    if (st == SQA_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(e, "sqa_create");
+    }
+    if (st != SQA_OK) {
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return SQA_OK;
+}
+
+void sqa_destroy(sqa_handle *h)
+{
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+}
+
+sqa_status sqa_get_info(const sqa_handle *h, sqa_info *o)
+{
+    if (!h || !o) return set_error("NULL argument"), SQA_ERR_INVALID;
+    o->n_phys = h->plan.n_phys;
+    o->n_used = h->plan.n;
+    o->n_terms = (int32_t)h->plan.terms.size();
+    o->z = h->job.Z;
+    o->words = h->job.W;
+    o->delta_min = h->dmin;
+    o->delta_max = h->dmax;
+    o->attempts_per_sweep = (int64_t)h->I * h->plan.n * h->job.Z * h->R;
+    o->device_bytes = h->device_bytes;
+    o->h2d_bytes = h->h2d_bytes;
+    o->launches_per_run = 2;  // init_kernel + sweep_kernel
+    o->pad_ = 0;
+    return SQA_OK;
+}
+
+sqa_status sqa_run_sweeps(sqa_handle *h, int32_t t0, int32_t t1, void *stream)
+{
+    if (!h || t0 < 0 || t1 < t0 || t1 > h->S) return set_error("sweep range"), SQA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    sqa_status st;
+    if (t0 == 0 && (st = launch_init(h, s)) != SQA_OK) return st;
+    if (t1 > t0) return launch_sweeps(h, t0, t1, 0, h->n_units, s);
+    return SQA_OK;
+}
+
+sqa_status sqa_run(sqa_handle *h, void *stream)
+{
+    if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
+    return sqa_run_sweeps(h, 0, h->S, stream);
+}
+
+sqa_status sqa_run_per_instance(sqa_handle *h, void *stream)
+{
+    if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    sqa_status st;
+    if ((st = launch_init(h, s)) != SQA_OK) return st;
+    int u = 0;
+    while (u < h->n_units) {
+        int v = u;
+        while (v < h->n_units && h->units[v].inst == h->units[u].inst) v++;
+        if ((st = launch_sweeps(h, 0, h->S, u, v - u, s)) != SQA_OK) return st;
+        u = v;
+    }
+    return SQA_OK;
+}
+
+sqa_status pt_run(sqa_handle *h, const double *betas, int32_t n_temps, int32_t n_sweeps,
+                  int32_t swap_every, void *stream)
+{
+    if (!h || !betas || n_temps < 1 || n_sweeps < 1 || swap_every < 1)
+        return set_error("pt_run arguments"), SQA_ERR_INVALID;
+    for (int p = 0; p < n_temps; p++)
+        if (!(betas[p] > 0) || !isfinite(betas[p])) return set_error("betas must be > 0"), SQA_ERR_INVALID;
+    for (int p = 0; p + 1 < n_temps; p++)
+        if (!(betas[p] > betas[p + 1])) return set_error("betas must decrease"), SQA_ERR_INVALID;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pt_run");
+    h->kind = SQA_KIND_PT;
+    h->P = n_temps;
+    h->betas.assign(betas, betas + n_temps);
+    h->S = n_sweeps;
+    h->swap_every = swap_every;
+    sqa_status st = setup_program(h);
+    if (st != SQA_OK) return st;
+    return sqa_run(h, stream);
+}
+
+sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
+{
+    if (!hs || n < 1) return set_error("batch arguments"), SQA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<JobDev> jobs;
+    std::vector<Unit> units;
+    int smem = 0;
+    sqa_status st;
+    for (int k = 0; k < n; k++) {
+        sqa_handle *h = hs[k];
+        if (!h) return set_error("NULL handle in batch"), SQA_ERR_INVALID;
+        if ((st = launch_init(h, s)) != SQA_OK) return st;
+        JobDev J = h->job;
+        J.t0 = 0;
+        J.t1 = h->S;
+        jobs.push_back(J);
+        smem = std::max(smem, J.smem_bytes);
+        for (Unit u : h->units) {
+            u.job = k;
+            units.push_back(u);
+        }
+    }
+    // longest units first so the tail of the launch is short
+    std::stable_sort(units.begin(), units.end(), [&](const Unit &a, const Unit &b) {
+        const JobDev &x = jobs[a.job], &y = jobs[b.job];
+        const double ca = (double)x.n * x.Z * a.wc * (x.t1 - x.t0);
+        const double cb = (double)y.n * y.Z * b.wc * (y.t1 - y.t0);
+        return ca > cb;
+    });
+    JobDev *d_jobs = nullptr;
+    Unit *d_units = nullptr;
+    int *d_counter = nullptr;
+    SQA_CUDA(cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(JobDev), s));
+    SQA_CUDA(cudaMallocAsync((void **)&d_units, units.size() * sizeof(Unit), s));
+    SQA_CUDA(cudaMallocAsync((void **)&d_counter, sizeof(int), s));
+    SQA_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, s));
+    SQA_CUDA(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s));
+    SQA_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
+    const int grid = grid_for(smem, (int)units.size());
+    sweep_kernel<<<grid, kThreads, smem, s>>>(d_jobs, d_units, (int)units.size(), d_counter);
+    SQA_CUDA(cudaGetLastError());
+    SQA_CUDA(cudaFreeAsync(d_jobs, s));
+    SQA_CUDA(cudaFreeAsync(d_units, s));
+    SQA_CUDA(cudaFreeAsync(d_counter, s));
+    // host vectors are consumed: pageable copies are staged before return
+    return SQA_OK;
+}
+
+static sqa_status to_out(void *dst, const void *dev_src, size_t bytes, int out_is_device, cudaStream_t s)
+{
+    SQA_CUDA(cudaMemcpyAsync(dst, dev_src, bytes, out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!out_is_device) SQA_CUDA(cudaStreamSynchronize(s));
+    return SQA_OK;
+}
+
+static sqa_status canon_out(sqa_handle *h, int z0, int zc, uint32_t *out, int out_is_device, void *stream)
+{
+    if (!h || !out) return set_error("NULL argument"), SQA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t count = (size_t)h->I * zc * h->job.n_phys * h->job.W;
+    uint32_t *dst = out;
+    if (!out_is_device) SQA_CUDA(cudaMallocAsync((void **)&dst, count * 4, s));
+    const int blocks = (int)std::min<size_t>((count + kThreads - 1) / kThreads, 8192);
+    canon_kernel<<<std::max(blocks, 1), kThreads, 0, s>>>(h->job, h->d_compact, z0, zc, dst);
+    SQA_CUDA(cudaGetLastError());
+    if (!out_is_device) {
+        sqa_status st = to_out(out, dst, count * 4, 0, s);
+        cudaFreeAsync(dst, s);
+        return st;
+    }
+    return SQA_OK;
+}
+
+sqa_status sqa_readout(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *stream)
+{
+    return canon_out(h, 0, 1, out, out_is_device, stream);
+}
+
+sqa_status sqa_state(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *stream)
+{
+    if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
+    return canon_out(h, 0, h->job.Z, out, out_is_device, stream);
+}
+
+sqa_status sqa_energies(sqa_handle *h, int32_t *out, int32_t out_is_device, void *stream)
+{
+    if (!h || !out) return set_error("NULL argument"), SQA_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t count = (size_t)h->I * h->job.Z * h->R;
+    int32_t *dst = out;
+    if (!out_is_device) SQA_CUDA(cudaMallocAsync((void **)&dst, count * 4, s));
+    const int blocks = (int)std::min<size_t>((count + kThreads - 1) / kThreads, 8192);
+    energy_kernel<<<std::max(blocks, 1), kThreads, 0, s>>>(h->job, dst);
+    SQA_CUDA(cudaGetLastError());
+    if (!out_is_device) {
+        sqa_status st = to_out(out, dst, count * 4, 0, s);
+        cudaFreeAsync(dst, s);
+        return st;
+    }
+    return SQA_OK;
+}
+
+sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *logical_out,
+                      int64_t *energy_out, const int64_t *e_ground, int32_t *success_out,
+                      int32_t out_is_device, void *stream)
+{
+    if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
+    const bool me = h->emb == SQA_EMB_ME_CHIMERA;
+    if (me != (method == SQA_DECODE_ME_MV) ||
+        (method < SQA_DECODE_ME_MV || method > SQA_DECODE_LHZ_CHAIN))
+        return set_error("decode method does not match the embedding"), SQA_ERR_INVALID;
+    if (method == SQA_DECODE_LHZ_TREES) {
+        if (n_trees == 0) {
+            n_trees = (h->N + 3) / 4 + 1;
+            if (n_trees % 2 == 0) n_trees++;
+        }
+        if (n_trees < 1 || n_trees > 1024) return set_error("n_trees"), SQA_ERR_INVALID;
+    } else {
+        n_trees = 1;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sqa_status st;
+    if (!me && (st = decode_trees(h, method, n_trees)) != SQA_OK) return st;
+    const size_t nrep = (size_t)h->I * h->R;
+    DecodeArgs D{};
+    D.method = method;
+    D.N = h->N;
+    D.n_trees = n_trees;
+    D.Lc = h->plan.Lc;
+    D.chain = h->d_chain;
+    D.pair = h->d_pair;
+    D.parents = h->d_parents;
+    D.orders = h->d_orders;
+    D.J = h->d_J;
+    int8_t *d_log = logical_out;
+    int64_t *d_en = energy_out, *d_eg = nullptr;
+    int32_t *d_succ = success_out;
+    if (!out_is_device) {
+        if (logical_out) SQA_CUDA(cudaMallocAsync((void **)&d_log, nrep * h->N, s));
+        if (energy_out) SQA_CUDA(cudaMallocAsync((void **)&d_en, nrep * 8, s));
+        if (success_out) SQA_CUDA(cudaMallocAsync((void **)&d_succ, (size_t)h->I * 4, s));
+    }
+    if (e_ground) {
+        SQA_CUDA(cudaMallocAsync((void **)&d_eg, (size_t)h->I * 8, s));
+        SQA_CUDA(cudaMemcpyAsync(d_eg, e_ground, (size_t)h->I * 8, cudaMemcpyHostToDevice, s));
+    }
+    if (d_succ) SQA_CUDA(cudaMemsetAsync(d_succ, 0, (size_t)h->I * 4, s));
+    D.logical = d_log;
+    D.energy = d_en;
+    D.e_ground = d_eg;
+    D.success = e_ground ? d_succ : nullptr;
+    const int blocks = (int)std::min<size_t>((nrep + 127) / 128, 8192);
+    decode_kernel<<<std::max(blocks, 1), 128, 0, s>>>(h->job, D);
+    SQA_CUDA(cudaGetLastError());
+    if (!out_is_device) {
+        if (logical_out) SQA_CUDA(cudaMemcpyAsync(logical_out, d_log, nrep * h->N, cudaMemcpyDeviceToHost, s));
+        if (energy_out) SQA_CUDA(cudaMemcpyAsync(energy_out, d_en, nrep * 8, cudaMemcpyDeviceToHost, s));
+        if (success_out) SQA_CUDA(cudaMemcpyAsync(success_out, d_succ, (size_t)h->I * 4, cudaMemcpyDeviceToHost, s));
+        SQA_CUDA(cudaStreamSynchronize(s));
+        if (logical_out) cudaFreeAsync(d_log, s);
+        if (energy_out) cudaFreeAsync(d_en, s);
+        if (success_out) cudaFreeAsync(d_succ, s);
+    }
+    if (d_eg) cudaFreeAsync(d_eg, s);
+    return SQA_OK;
+}
+
+sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, int64_t *e_out)
+{
+    if (N < 2 || N > 40 || n_instances < 1 || !J || !e_out) return set_error("ground arguments"), SQA_ERR_INVALID;
+    sqa_status st = device_ready();
+    if (st != SQA_OK) return st;
+    const size_t npair = (size_t)N * (N - 1) / 2;
+    int32_t *dJ = nullptr;
+    unsigned long long *dbest = nullptr;
+    SQA_CUDA(cudaMalloc(&dJ, npair * n_instances * 4));
+    cudaError_t e = cudaMalloc(&dbest, (size_t)n_instances * 8);
+    if (e != cudaSuccess) {
+        cudaFree(dJ);
+        return cuda_fail(e, "cudaMalloc");
+    }
+    cudaMemcpy(dJ, J, npair * n_instances * 4, cudaMemcpyHostToDevice);
+    cudaMemset(dbest, 0xFF, (size_t)n_instances * 8);
+    const int total_bits = N - 1;
+    const int chunk_bits = std::max(0, std::min(total_bits, total_bits - 17));
+    const int64_t n_chunks = (int64_t)1 << (total_bits - chunk_bits);
+    const int bx = (int)std::min<int64_t>((n_chunks + 127) / 128, 2048);
+    ground_kernel<<<dim3(std::max(bx, 1), n_instances), 128>>>(N, dJ, chunk_bits, n_chunks, dbest);
+    e = cudaGetLastError();
+    std::vector<unsigned long long> best(n_instances);
+    if (e == cudaSuccess) e = cudaMemcpy(best.data(), dbest, (size_t)n_instances * 8, cudaMemcpyDeviceToHost);
+    cudaFree(dJ);
+    cudaFree(dbest);
+    if (e != cudaSuccess) return cuda_fail(e, "ground_kernel");
+    for (int i = 0; i < n_instances; i++) e_out[i] = (int64_t)(best[i] ^ 0x8000000000000000ull);
+    return SQA_OK;
+}
+
+sqa_status sqa_plan_terms(int32_t embedding, int32_t N, const int32_t *J, int32_t penalty,
+                          int32_t cap_terms, int32_t *n_phys, int32_t *n_terms,
+                          int32_t *term_size, int32_t *term_mem, int32_t *term_w,
+                          int32_t *colour)
+{
+    if (N < 2 || N > kMaxN || !J || !n_phys || !n_terms) return set_error("plan_terms arguments"), SQA_ERR_INVALID;
+    Plan pl;
+    std::string err;
+    if (!build_plan(embedding, N, pl, err)) return set_error(err), SQA_ERR_INVALID;
+    *n_phys = pl.n_phys;
+    *n_terms = (int32_t)pl.terms.size();
+    if ((int)pl.terms.size() > cap_terms) return set_error("cap_terms too small"), SQA_ERR_INVALID;
+    for (size_t t = 0; t < pl.terms.size(); t++) {
+        const PlanTerm &x = pl.terms[t];
+        if (term_size) term_size[t] = x.size;
+        if (term_mem)
+            for (int k = 0; k < 4; k++) term_mem[t * 4 + k] = k < x.size ? x.mem[k] : -1;
+        if (term_w) term_w[t] = x.jidx >= 0 ? J[x.jidx] : -penalty;
+    }
+    if (colour) {
+        for (int s = 0; s < pl.n_phys; s++) colour[s] = -1;
+        for (int c = 0; c < pl.ncol; c++)
+            for (int i = pl.col_ptr[c]; i < pl.col_ptr[c + 1]; i++) colour[pl.canon[i]] = c;
+    }
+    return SQA_OK;
+}
+
+sqa_status sqa_plan_tables(const sqa_desc *d, uint32_t *T, int64_t cap, int32_t *dmin_out,
+                           int32_t *dmax_out)
+{
+    sqa_status st = validate(d);
+    if (st != SQA_OK) return st;
+    Plan pl;
+    std::string err;
+    if (!build_plan(d->embedding, d->n_logical, pl, err)) return set_error(err), SQA_ERR_INVALID;
+    const int npair = d->n_logical * (d->n_logical - 1) / 2;
+    int smax = 0;
+    for (int i = 0; i < d->n_instances; i++)
+        smax = std::max(smax, site_weight_sum_max(pl, d->J + (size_t)i * npair, d->penalty));
+    const int dmin = -2 * smax, dmax = 2 * smax;
+    std::vector<uint32_t> tab;
+    if (d->kind == SQA_KIND_SQA) {
+        std::vector<double> A(d->n_sweeps), B(d->n_sweeps);
+        for (int t = 0; t < d->n_sweeps; t++) {
+            const double s = ((double)t + 0.5) / (double)d->n_sweeps;
+            A[t] = d->A ? d->A[t] : 1.0 - s;
+            B[t] = d->B ? d->B[t] : s;
+        }
+        sqa_tables(A.data(), B.data(), d->beta, d->n_slices, d->n_sweeps, dmin, dmax, tab);
+    } else {
+        pt_tables(d->betas, d->n_temps, dmin, dmax, tab);
+    }
+    if (dmin_out) *dmin_out = dmin;
+    if (dmax_out) *dmax_out = dmax;
+    if (!T) return SQA_OK;
+    if ((int64_t)tab.size() > cap) return set_error("cap too small"), SQA_ERR_INVALID;
+    memcpy(T, tab.data(), tab.size() * 4);
+    return SQA_OK;
+}
+
+sqa_status sqa_plan_swap_table(const double *betas, int32_t n_temps, int32_t pair, uint32_t *out,
+                               int32_t cap, int32_t *len)
+{
+    if (!betas || n_temps < 2 || pair < 0 || pair + 1 >= n_temps || !len) return set_error("swap table arguments"), SQA_ERR_INVALID;
+    std::vector<uint32_t> T;
+    std::vector<int> off, ln;
+    swap_tables(betas, n_temps, T, off, ln);
+    *len = ln[pair];
+    if (!out) return SQA_OK;
+    if (ln[pair] > cap) return set_error("cap too small"), SQA_ERR_INVALID;
+    memcpy(out, T.data() + off[pair], (size_t)ln[pair] * 4);
+    return SQA_OK;
+}
+
+sqa_status sqa_plan_tree(int32_t N, uint64_t seed, int32_t inst, int32_t tree, int32_t *parent)
+{
+    if (N < 2 || N > kMaxN || !parent || inst < 0 || tree < 0) return set_error("tree arguments"), SQA_ERR_INVALID;
+    std::vector<int> order(N), par(N);
+    prufer_tree(N, seed, inst, tree, par.data(), order.data());
+    for (int v = 0; v < N; v++) parent[v] = par[v];
+    return SQA_OK;
+}
+
+}  // extern "C"

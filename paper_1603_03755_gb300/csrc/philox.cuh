@@ -1,0 +1,65 @@
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror and Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC'11), restated for the
+// library: ten rounds, multipliers 0xD2511F53 / 0xCD9E8D57, key bumped by the
+// Weyl constants 0x9E3779B9 / 0xBB67AE85 between rounds.  Usable from host
+// code (tree draws) and device code (the sweeps).
+//
+// Streams: key = (seed_lo, seed_hi ^ domain).  The domain words and the
+// counter layout of every stream are part of the library's definition of the
+// Markov chain; they are restated, not shared, by the CPU checker.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define SQA_HD __host__ __device__ __forceinline__
+#else
+#define SQA_HD inline
+#endif
+
+namespace sqa {
+
+constexpr uint32_t kDomInit = 0x6A09E667u;
+constexpr uint32_t kDomSweepHi = 0xBB67AE85u;
+constexpr uint32_t kDomSweepLo = 0x3C6EF372u;
+constexpr uint32_t kDomSwap = 0xA54FF53Au;
+constexpr uint32_t kDomTree = 0x510E527Fu;
+
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+SQA_HD uint32_t mulhi32(uint32_t a, uint32_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+// One Philox4x32-10 block.  The key schedule k + r*W is formed per round.
+SQA_HD U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1)
+{
+#if defined(__CUDA_ARCH__)
+#pragma unroll
+#endif
+    for (int r = 0; r < 10; r++) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = mulhi32(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = mulhi32(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+SQA_HD uint32_t word_of(const U4 &v, int i)
+{
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+}  // namespace sqa

@@ -1,0 +1,231 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Spins, energies, decoded states and success counts are compared bit for bit
+(integer work: the tolerance is zero).  Sizes are small enough for the oracle
+to finish in seconds but span several classes, words and a ragged replica
+tail; the edge cases cover L = 2, one physical spin, a partial Chimera group,
+an infinite Jperp (A = 0), PT with one slot, and a full-size launch checked
+on sampled replicas.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1603_03755_gb300 as pkg
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_state(h):
+    st = h.state(stream=0)                      # [I][Z][n_phys][W]
+    return pkg.unpack_words(st, h.R)            # [I][Z][n_phys][R]
+
+
+def oracle_sqa(emb, N, J, pen, L, R, beta, S, seed, inst=0, A=None, B=None, t1=None, rho=None):
+    pb = O.Problem(emb, N, J, pen)
+    if A is None:
+        A, B = O.linear_schedule(S)
+    q = O.SQA(pb, L, R, beta, A, B, seed, inst)
+    r0, r1 = rho if rho is not None else (0, R)
+    q.run(0, S if t1 is None else t1, r0, r1)
+    return pb, q
+
+
+def sqa_case(emb, N, I, L, R, S, pen, beta, seed, A=None, B=None):
+    J = W.random_instances(N, I, seed)
+    h = pkg.Handle(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=seed, L=L, beta=beta,
+                   A=A, B=B)
+    h.run(stream=0)
+    got = gpu_state(h)
+    for i in range(I):
+        pb, q = oracle_sqa(emb, N, J[i], pen, L, R, beta, S, seed, i, A, B)
+        assert np.array_equal(got[i], q.s), f"instance {i}: state differs"
+    return h, J, got
+
+
+def test_sqa_lhz_k6_l32_r64_s1000():
+    """LHZ K_6: 15 spins, 10 plaquettes, C = 3 max|J|, beta = 10/max|J|, L = 32, R = 64, 1000 sweeps."""
+    c = W.lhz_n6_config()
+    h = pkg.Handle(embedding="lhz", N=c["N"], J=c["J"], penalty=c["penalty"], sweeps=c["sweeps"],
+                   R=c["R"], seed=c["seed"], L=c["L"], beta=c["beta"])
+    h.run(stream=0)
+    got = gpu_state(h)
+    pb, q = oracle_sqa("lhz", c["N"], c["J"][0], c["penalty"], c["L"], c["R"], c["beta"],
+                       c["sweeps"], c["seed"])
+    assert np.array_equal(got[0], q.s)
+    E = h.energies(stream=0)[0]
+    assert np.array_equal(E, q.slice_energies())
+    ro = pkg.unpack_words(h.readout(stream=0), c["R"])[0]
+    assert np.array_equal(ro, q.s[0])
+
+
+@pytest.mark.parametrize("emb,N,I,L,R,S", [("me", 8, 3, 8, 80, 40), ("lhz", 8, 2, 16, 70, 30),
+                                           ("me", 12, 2, 6, 40, 25), ("lhz", 5, 2, 4, 129, 20)])
+def test_sqa_multi_instance_ragged_replicas(emb, N, I, L, R, S):
+    pen = 6 if emb == "me" else 9
+    h, J, got = sqa_case(emb, N, I, L, R, S, pen, 10 / 3, seed=11 + N)
+    E = h.energies(stream=0)
+    for i in range(I):
+        pb = O.Problem(emb, N, J[i], pen)
+        for z in range(L):
+            assert np.array_equal(E[i, z], pb.energies(got[i, z]))
+
+
+@pytest.mark.parametrize("emb,N,L,R,S", [("me", 4, 2, 33, 30),      # L = 2: both neighbours one slice
+                                         ("lhz", 2, 6, 5, 30),      # one physical spin, no plaquette
+                                         ("me", 5, 4, 32, 15),      # partial Chimera group
+                                         ("me", 2, 4, 1, 10)])      # one replica
+def test_sqa_edge_shapes(emb, N, L, R, S):
+    sqa_case(emb, N, 2, L, R, S, 4, 1.3, seed=5)
+
+
+def test_sqa_user_schedule_reaching_zero_field():
+    S = 24
+    A = np.linspace(1.0, 0.0, S)     # last sweep: A = 0, Jperp infinite
+    B = np.linspace(0.05, 1.0, S)
+    sqa_case("lhz", 4, 2, 6, 48, S, 3, 2.0, seed=3, A=A, B=B)
+
+
+def test_resume_equals_one_run():
+    emb, N, L, R, S, pen = "me", 8, 8, 64, 50, 6
+    J = W.random_instances(N, 2, 4)
+    a = pkg.Handle(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=4, L=L, beta=3.0)
+    a.run(stream=0)
+    b = pkg.Handle(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=4, L=L, beta=3.0)
+    b.run_sweeps(0, 17, stream=0)
+    b.run_sweeps(17, 18, stream=0)
+    b.run_sweeps(18, S, stream=0)
+    assert np.array_equal(a.state(stream=0), b.state(stream=0))
+
+
+def test_per_instance_path_equals_batched():
+    emb, N, L, R, S, pen = "lhz", 7, 8, 96, 20, 9
+    J = W.random_instances(N, 5, 8)
+    a = pkg.Handle(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=8, L=L, beta=3.0)
+    a.run(stream=0)
+    b = pkg.Handle(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=8, L=L, beta=3.0)
+    b.run_per_instance(stream=0)
+    assert np.array_equal(a.state(stream=0), b.state(stream=0))
+
+
+def test_batch_run_ragged_mix_equals_alone():
+    specs = [dict(embedding="lhz", N=8, L=32, R=128, penalty=9, kind="sqa"),
+             dict(embedding="me", N=12, L=16, R=40, penalty=6, kind="sqa"),
+             dict(embedding="me", N=5, R=64, penalty=6, kind="pt"),
+             dict(embedding="lhz", N=10, L=8, R=32, penalty=9, kind="sqa")]
+    mk = []
+    for k, s in enumerate(specs):
+        J = W.random_instances(s["N"], 2, 100 + k)
+        kw = dict(embedding=s["embedding"], N=s["N"], J=J, penalty=s["penalty"], sweeps=15, R=s["R"],
+                  seed=100 + k, kind=s["kind"])
+        if s["kind"] == "sqa":
+            kw.update(L=s["L"], beta=3.0)
+        else:
+            kw.update(betas=W.geometric_ladder(6, 4.0, 0.3), swap_every=2)
+        mk.append(kw)
+    alone = []
+    for kw in mk:
+        h = pkg.Handle(**kw)
+        h.run(stream=0)
+        alone.append(h.state(stream=0))
+    mixed = [pkg.Handle(**kw) for kw in mk]
+    pkg.batch_run(mixed, stream=0)
+    for a, h in zip(alone, mixed):
+        assert np.array_equal(a, h.state(stream=0))
+
+
+@pytest.mark.parametrize("emb,N,P,R,S,swap", [("me", 5, 6, 40, 31, 3), ("lhz", 6, 8, 64, 20, 1),
+                                              ("me", 8, 1, 32, 12, 1), ("lhz", 4, 2, 100, 25, 2)])
+def test_pt_parity(emb, N, P, R, S, swap):
+    pen = 6 if emb == "me" else 9
+    J = W.random_instances(N, 2, 21)
+    betas = W.geometric_ladder(P, 5.0, 0.2)
+    h = pkg.Handle(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=21, kind="pt",
+                   betas=betas, swap_every=swap)
+    h.run(stream=0)
+    got = gpu_state(h)
+    E = h.energies(stream=0)
+    for i in range(2):
+        pb = O.Problem(emb, N, J[i], pen)
+        o = O.PT(pb, betas, R, swap, 21, i)
+        o.run(0, S)
+        assert np.array_equal(got[i], o.s), f"instance {i}"
+        assert np.array_equal(E[i], o.E)
+
+
+def test_pt_run_entry_point():
+    N, R = 6, 32
+    J = W.random_instances(N, 1, 2)
+    h = pkg.Handle(embedding="me", N=N, J=J, penalty=6, sweeps=10, R=R, seed=2, L=4, beta=2.0)
+    betas = W.paper_beta_ladder(8, 20.0, 0.1)
+    h.pt_run(betas, 14, 10, stream=0)
+    got = gpu_state(h)
+    o = O.PT(O.Problem("me", N, J[0], 6), betas, R, 10, 2, 0)
+    o.run(0, 14)
+    assert np.array_equal(got[0], o.s)
+
+
+def _oracle_decode(pb, method, phys, seed, inst, n_trees):
+    N = pb.N
+    if method == "me_mv":
+        return O.me_decode(pb, phys)
+    if method == "lhz_star":
+        return O.lhz_tree_decode(N, O.star_tree(N), phys)
+    if method == "lhz_chain":
+        return O.lhz_tree_decode(N, O.chain_tree(N), phys)
+    trees = np.stack([O.prufer_tree(N, seed, inst, t) for t in range(n_trees)])
+    return O.lhz_vote_decode(N, trees, phys)
+
+
+@pytest.mark.parametrize("emb,method,N", [("me", "me_mv", 8), ("me", "me_mv", 12),
+                                          ("lhz", "lhz_trees", 8), ("lhz", "lhz_star", 6),
+                                          ("lhz", "lhz_chain", 7)])
+def test_decode_parity(emb, method, N):
+    I, R, L, S = 3, 70, 8, 30
+    pen = 6 if emb == "me" else 9
+    J = W.random_instances(N, I, 31)
+    h = pkg.Handle(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=31, L=L, beta=3.0)
+    h.run(stream=0)
+    phys = pkg.unpack_words(h.readout(stream=0), R)     # [I][n_phys][R]
+    eg = np.array([O.ground_energy(N, J[i])[0] for i in range(I)], np.int64)
+    n_trees = O.default_n_trees(N)
+    logical, energy, succ = h.decode(method, 0, e_ground=eg, stream=0)
+    for i in range(I):
+        pb = O.Problem(emb, N, J[i], pen)
+        cnt = 0
+        for r in range(R):
+            want = _oracle_decode(pb, method, phys[i, :, r], 31, i, n_trees)
+            assert np.array_equal(logical[i, r], want), (i, r)
+            e = O.logical_energy(N, J[i], want)
+            assert energy[i, r] == e
+            cnt += e == eg[i]
+        assert succ[i] == cnt
+
+
+@pytest.mark.parametrize("N", [2, 3, 5, 8, 11, 16])
+def test_ground_energy_parity(N):
+    J = W.random_instances(N, 4, 50 + N)
+    got = pkg.ground_energy(N, J)
+    want = [O.ground_energy(N, J[i])[0] for i in range(4)]
+    assert list(got) == want
+
+
+def test_full_size_me_k8_batch_sampled():
+    """The benchmark's workload and launch: ME K_8, 1024 instances x 256
+    replicas, L = 64, 1e4 sweeps, one persistent launch.  Sampled replicas of
+    the first and last instance are re-run by the oracle; every sampled
+    energy is recomputed from the spins."""
+    c = W.me_n8_batch_config()
+    h = pkg.Handle(embedding="me", N=c["N"], J=c["J"], penalty=c["penalty"], sweeps=c["sweeps"],
+                   R=c["R"], seed=c["seed"], L=c["L"], beta=c["beta"])
+    h.run(stream=0)
+    st = h.state(stream=0)
+    E = h.energies(stream=0)
+    for inst, (r0, r1) in [(0, (0, 6)), (1023, (250, 256))]:
+        pb, q = oracle_sqa("me", c["N"], c["J"][inst], c["penalty"], c["L"], c["R"], c["beta"],
+                           c["sweeps"], c["seed"], inst, rho=(r0, r1))
+        got = pkg.unpack_words(st[inst], c["R"])
+        assert np.array_equal(got[:, :, r0:r1], q.s[:, :, r0:r1])
+        for z in (0, 31, 63):
+            assert np.array_equal(E[inst, z, r0:r1], pb.energies(got[z])[r0:r1])
