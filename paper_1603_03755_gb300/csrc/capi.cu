@@ -37,9 +37,9 @@ static sqa_status cuda_fail(cudaError_t e, const char *where)
     } while (0)
 
 constexpr int kThreads = 256;
-constexpr int kSmemLimit = 227 * 1024;
 
 static int g_num_sms = 0;
+static int g_smem_limit = 0;  // dynamic shared memory one sweep block may use
 
 static sqa_status device_ready()
 {
@@ -53,8 +53,12 @@ static sqa_status device_ready()
     if (g_num_sms == 0) {
         cudaDeviceProp prop;
         SQA_CUDA(cudaGetDeviceProperties(&prop, dev));
+        cudaFuncAttributes fa;
+        SQA_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel));
+        const int limit = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
+        SQA_CUDA(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
         g_num_sms = prop.multiProcessorCount;
-        SQA_CUDA(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        g_smem_limit = limit;
     }
     return SQA_OK;
 }
@@ -161,10 +165,10 @@ int unit_smem(const JobDev &J, int wc, int *zstride_out)
 
 // Choose the words per unit: as many as fit a shared-memory budget that
 // leaves room for two resident blocks.
-void plan_units(sqa_handle *h)
+sqa_status plan_units(sqa_handle *h)
 {
     JobDev &J = h->job;
-    const int budget = kSmemLimit / 2 - 1024;
+    const int budget = g_smem_limit / 2 - 1024;
     int wc = J.W, zs = 0;
     while (wc > 1 && unit_smem(J, wc, &zs) > budget) wc = (wc + 1) / 2;
     J.smem_bytes = unit_smem(J, wc, &zs);
@@ -173,6 +177,11 @@ void plan_units(sqa_handle *h)
     h->units.clear();
     for (int i = 0; i < h->I; i++)
         for (int w0 = 0; w0 < J.W; w0 += wc) h->units.push_back(Unit{0, i, w0, std::min(wc, J.W - w0)});
+    if (J.smem_bytes > g_smem_limit) {
+        set_error("one word of this problem does not fit in shared memory");
+        return SQA_ERR_UNSUPPORTED;
+    }
+    return SQA_OK;
 }
 
 sqa_status validate(const sqa_desc *d)
@@ -290,7 +299,7 @@ sqa_status setup_program(sqa_handle *h)
     J.Tsw = h->d_Tsw;
     J.sw_off = h->d_swoff;
     J.sw_len = h->d_swlen;
-    plan_units(h);
+    if ((st = plan_units(h)) != SQA_OK) return st;
     if ((st = dalloc(h, &h->d_job, 1)) != SQA_OK) return st;
     if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) return st;
     h->n_units = (int)h->units.size();
