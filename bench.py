@@ -316,6 +316,7 @@ def main():
     f_mhz = (clk or {}).get("sm_mhz") or 1462.0
     peaks, src = load_peaks()
     peak_gops = n_sm * 4 * 32 * f_mhz * 1e6 / 1e9
+    intpeak = {k: round(pkg.int_peak(k), 2) for k in pkg.INT_PEAK_KINDS}
     t_sweep = statistics.mean(sweep_times)
     achieved_gops = attempts * OPS_PER_ATTEMPT / t_sweep / 1e9
     cpu = None
@@ -333,7 +334,8 @@ def main():
                      "frac": achieved_gops / peak_gops, "traffic": None,
                      "kernel": "sweep_kernel", "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_basis": f"{n_sm} SMs x 4 SMSP x 32 lanes x {f_mhz:.0f} MHz (median SM clock under load)",
-                     "sweep_kernel_s": t_sweep},
+                     "sweep_kernel_s": t_sweep,
+                     "measured_lane_ops_per_sm_clk": intpeak},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches_per_step * args.steps,

@@ -112,6 +112,16 @@ sqa_status sqa_create(const sqa_desc *desc, sqa_handle **out);
 void sqa_destroy(sqa_handle *h);
 sqa_status sqa_get_info(const sqa_handle *h, sqa_info *out);
 
+/* Launch shape of the sweep kernel (the autotuner's knobs; results do not
+ * depend on them).  words_per_unit: 32-replica words one block holds
+ * (0 = automatic).  use_table: SQA threshold lookup through per-site code
+ * tables (1), byte-wise index windows (0), or automatic (-1); PT always uses
+ * windows.  Fails with SQA_ERR_UNSUPPORTED, leaving the shape unchanged, when
+ * the request does not fit in shared memory.  Synchronizes the device. */
+sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table);
+sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t *use_table,
+                          int32_t *smem_bytes);
+
 /* Runs the whole program: fresh initial spins, then sweeps 0..S-1 (SQA
  * anneal, or PT with swaps every swap_every sweeps), as one persistent
  * launch over all instances.  Asynchronous on stream. */
@@ -184,6 +194,14 @@ sqa_status sqa_plan_swap_table(const double *betas, int32_t n_temps, int32_t pai
 /* The random spanning tree number `tree` of instance `inst` used by
  * SQA_DECODE_LHZ_TREES: parent[v], parent[0] = -1. */
 sqa_status sqa_plan_tree(int32_t N, uint64_t seed, int32_t inst, int32_t tree, int32_t *parent);
+
+/* Diagnostic: sustained integer instructions per SM clock (all lanes) of one
+ * instruction kind on the current device, from a dependency-free
+ * microbenchmark timed with the SM clock counter.  kind: 0 LOP3, 1 IADD3,
+ * 2 IMAD, 3 IMAD.WIDE, 4 IMAD.HI, 5 LOP3/IMAD alternating, 6 Philox4x32-10
+ * blocks (result in blocks, not instructions), 7 the same with one
+ * 32x32->64 multiply per product.  Synchronous. */
+sqa_status sqa_int_peak(int32_t kind, double *lane_ops_per_clk_per_sm);
 
 const char *sqa_strerror(sqa_status s);
 /* Detail of the last error on this thread (CUDA message, bad field). */

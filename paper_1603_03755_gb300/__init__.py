@@ -53,6 +53,8 @@ _SIGS = {
     "sqa_create": (C.c_int, [C.POINTER(_Desc), C.POINTER(C.c_void_p)]),
     "sqa_destroy": (None, [C.c_void_p]),
     "sqa_get_info": (C.c_int, [C.c_void_p, C.POINTER(_Info)]),
+    "sqa_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "sqa_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "sqa_run": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sqa_run_sweeps": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     "sqa_run_per_instance": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -69,6 +71,7 @@ _SIGS = {
     "sqa_plan_tables": (C.c_int, [C.POINTER(_Desc), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "sqa_plan_swap_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     "sqa_plan_tree": (C.c_int, [C.c_int32, C.c_uint64, C.c_int32, C.c_int32, C.c_void_p]),
+    "sqa_int_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
     "sqa_strerror": (C.c_char_p, [C.c_int]),
     "sqa_last_error": (C.c_char_p, []),
 }
@@ -163,6 +166,15 @@ class Handle:
 
     __del__ = close
 
+    # ---- launch shape ----
+    def tune(self, words_per_unit: int = 0, use_table: int = -1):
+        _check(lib().sqa_tune(self._h, words_per_unit, use_table), "sqa_tune")
+
+    def launch(self) -> dict:
+        wc, lut, smem = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().sqa_get_launch(self._h, C.byref(wc), C.byref(lut), C.byref(smem)), "sqa_get_launch")
+        return {"words_per_unit": wc.value, "use_table": lut.value, "smem_bytes": smem.value}
+
     # ---- running ----
     def run(self, stream=None):
         _check(lib().sqa_run(self._h, _stream_ptr(stream)), "sqa_run")
@@ -238,6 +250,17 @@ def ground_energy(N: int, J) -> np.ndarray:
     out = np.zeros(J.shape[0], np.int64)
     _check(lib().sqa_ground_energy(N, J.shape[0], J.ctypes.data, out.ctypes.data), "sqa_ground_energy")
     return out
+
+
+INT_PEAK_KINDS = ("lop3", "iadd3", "imad", "imad_wide", "imad_hi", "lop3_imad", "philox_blocks",
+                  "philox_wide_blocks")
+
+
+def int_peak(kind: str) -> float:
+    """Measured integer lane-ops per SM clock for one instruction kind."""
+    v = C.c_double()
+    _check(lib().sqa_int_peak(INT_PEAK_KINDS.index(kind), C.byref(v)), "sqa_int_peak")
+    return v.value
 
 
 def unpack_words(words, R: int) -> np.ndarray:

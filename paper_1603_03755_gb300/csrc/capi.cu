@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "layout.cuh"
 #include "philox.cuh"
 #include "sqa_internal.h"
 
@@ -15,6 +16,12 @@ namespace sqa {
 
 __global__ void init_kernel(JobDev J, const int *canon);
 __global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units, int *counter);
+// The single-job sweep kernel (kernels.cu), one instantiation per path.
+const void *sweep_one_entry(const JobDev &J);
+const void *sweep_one_entry_mode(int mode);
+cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, int *counter, int grid,
+                             cudaStream_t s);
+static const void *one_kernel(const JobDev &J) { return sweep_one_entry(J); }
 __global__ void energy_kernel(JobDev J, int32_t *out);
 __global__ void canon_kernel(JobDev J, const int *compact_of, int z0, int zcount, uint32_t *out);
 __global__ void decode_kernel(JobDev J, DecodeArgs D);
@@ -55,8 +62,15 @@ static sqa_status device_ready()
         SQA_CUDA(cudaGetDeviceProperties(&prop, dev));
         cudaFuncAttributes fa;
         SQA_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel));
-        const int limit = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
-        SQA_CUDA(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+        const void *ks[4] = {(const void *)sweep_kernel, sweep_one_entry_mode(0), sweep_one_entry_mode(1),
+                             sweep_one_entry_mode(2)};
+        int limit = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
+        for (const void *k : ks) {
+            cudaFuncAttributes fk;
+            SQA_CUDA(cudaFuncGetAttributes(&fk, k));
+            limit = std::min(limit, (int)prop.sharedMemPerBlockOptin - (int)fk.sharedSizeBytes);
+        }
+        for (const void *k : ks) SQA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
         g_num_sms = prop.multiProcessorCount;
         g_smem_limit = limit;
     }
@@ -76,6 +90,8 @@ struct sqa_handle {
     std::vector<double> A, B, betas;
     Plan plan;
     int smax = 0, dmin = 0, dmax = 0, nd = 0;
+    bool window_limit_exceeded = false;
+    int force_wc = 0, force_mode = -1;  // sqa_tune overrides (0 / -1: automatic)
     // device
     JobDev job{};
     uint32_t *d_state = nullptr;
@@ -130,18 +146,19 @@ sqa_status upload(sqa_handle *h, T **p, const std::vector<T> &v)
 
 void free_all(sqa_handle *h)
 {
-    for (void *p : h->allocs) cudaFree(p);
+    for (void *p : h->allocs)
+        if (p) cudaFree(p);
     h->allocs.clear();
     h->device_bytes = 0;
     h->h2d_bytes = 0;
 }
 
-// Shared memory of one unit of wc words.
-int unit_smem(const JobDev &J, int wc, int *zstride_out)
+// Row stride (words) of the shared state for units of wc words: consecutive
+// lanes take consecutive words, then the next z step (two slices for SQA, one
+// slot for PT); pad the row so those lanes fall on distinct banks.
+int zstride_for(const JobDev &J, int wc)
 {
     int zs = J.n * wc;
-    // items of consecutive lanes differ by one word, then by one z step
-    // (SQA steps two slices); pad the row so lanes fall on distinct banks
     if (J.kind == SQA_KIND_SQA) {
         if (wc % 2 == 0) {
             while ((2 * zs) % 32 != wc % 32) zs++;
@@ -151,36 +168,67 @@ int unit_smem(const JobDev &J, int wc, int *zstride_out)
     } else {
         while (zs % 32 != wc % 32) zs++;
     }
-    *zstride_out = zs;
-    size_t off = (size_t)J.Z * zs * 4;
-    off += (size_t)(J.kind == SQA_KIND_SQA ? J.nrow : J.Z * J.nrow) * 4;
-    off = (off + 15) & ~(size_t)15;
-    off += (size_t)J.n * sizeof(SiteRec);
-    if (J.kind == SQA_KIND_PT) {
-        off += (size_t)J.Z * wc * 32 * 4;
-        off += (size_t)(J.Z / 2 + 1) * wc * 4;
-    }
-    return (int)off;
+    return zs;
 }
 
-// Choose the words per unit: as many as fit a shared-memory budget that
-// leaves room for two resident blocks.
+int unit_smem(const JobDev &J, int wc, int *zstride_out)
+{
+    const int zs = zstride_for(J, wc);
+    *zstride_out = zs;
+    return (int)smem_layout(J, wc, zs).total;
+}
+
+int blocks_per_sm(const void *kernel, int smem)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm;
+}
+
+// Choose the words per unit (and, for SQA, table or window mode): the most
+// resident blocks per SM first, then the most words per unit.
 sqa_status plan_units(sqa_handle *h)
 {
     JobDev &J = h->job;
-    const int budget = g_smem_limit / 2 - 1024;
-    int wc = J.W, zs = 0;
-    while (wc > 1 && unit_smem(J, wc, &zs) > budget) wc = (wc + 1) / 2;
-    J.smem_bytes = unit_smem(J, wc, &zs);
-    J.zstride = zs;
-    J.wc = wc;
-    h->units.clear();
-    for (int i = 0; i < h->I; i++)
-        for (int w0 = 0; w0 < J.W; w0 += wc) h->units.push_back(Unit{0, i, w0, std::min(wc, J.W - w0)});
-    if (J.smem_bytes > g_smem_limit) {
-        set_error("one word of this problem does not fit in shared memory");
+    int best_wc = 0, best_blocks = 0, best_lut = 0;
+    const int modes = J.kind == SQA_KIND_SQA ? 2 : 1;
+    for (int m = modes - 1; m >= 0; m--) {
+        J.use_lut = J.kind == SQA_KIND_SQA ? m : 0;
+        if (!J.use_lut && h->window_limit_exceeded) continue;
+        if (h->force_mode >= 0 && J.kind == SQA_KIND_SQA && J.use_lut != h->force_mode) continue;
+        for (int wc = J.W; wc >= 1; wc = wc > 1 ? (wc + 1) / 2 : 0) {
+            if (h->force_wc > 0 && wc != std::min(h->force_wc, J.W)) {
+                if (wc == 1) break;
+                continue;
+            }
+            int zs = 0;
+            const int smem = unit_smem(J, wc, &zs);
+            if (smem > g_smem_limit) continue;
+            J.smem_bytes = smem;
+            J.wc = wc;
+            J.zstride = zs;
+            const int blocks = std::min(blocks_per_sm(one_kernel(J), smem), 3);
+            if (blocks > best_blocks) {
+                best_blocks = blocks;
+                best_wc = wc;
+                best_lut = J.use_lut;
+            }
+            if (wc == 1) break;
+        }
+    }
+    if (best_blocks == 0) {
+        set_error("the requested unit does not fit in shared memory");
         return SQA_ERR_UNSUPPORTED;
     }
+    J.use_lut = best_lut;
+    J.wc = best_wc;
+    J.smem_bytes = unit_smem(J, best_wc, &J.zstride);
+    h->units.clear();
+    for (int i = 0; i < h->I; i++)
+        for (int w0 = 0; w0 < J.W; w0 += J.wc) h->units.push_back(Unit{0, i, w0, std::min(J.wc, J.W - w0)});
     return SQA_OK;
 }
 
@@ -227,8 +275,15 @@ sqa_status setup_program(sqa_handle *h)
     for (int i = 0; i < h->I; i++)
         h->smax = std::max(h->smax, site_weight_sum_max(pl, h->J.data() + (size_t)i * npair, h->penalty));
     const int K = h->kind == SQA_KIND_SQA ? 6 : 2;
-    if (K * h->smax + 2 > kMaxByteWindow) {
+    // byte-wise windows hold K*S_i (+2 for SQA) per site; the SQA table mode
+    // has no such limit
+    h->window_limit_exceeded = K * h->smax + 2 > kMaxByteWindow;
+    if (h->window_limit_exceeded && h->kind == SQA_KIND_PT) {
         set_error("penalty/couplings too large for the byte-wise threshold window");
+        return SQA_ERR_UNSUPPORTED;
+    }
+    if (3 * h->smax + 8 > 32767) {
+        set_error("penalty/couplings too large");
         return SQA_ERR_UNSUPPORTED;
     }
     h->dmin = -2 * h->smax;
@@ -258,6 +313,8 @@ sqa_status setup_program(sqa_handle *h)
 
     std::vector<SiteRec> sites, all_sites;
     std::vector<ETerm> et, all_et;
+    J.lut_entries = 0;
+    for (int i = 0; i < pl.n; i++) J.lut_entries += 1 << ((int)pl.site_terms[i].size() + 2);
     for (int i = 0; i < h->I; i++) {
         const int32_t *Ji = h->J.data() + (size_t)i * npair;
         build_sites(pl, Ji, h->penalty, K, h->smax, sites);
@@ -316,11 +373,9 @@ sqa_status launch_init(sqa_handle *h, cudaStream_t s)
     return SQA_OK;
 }
 
-int grid_for(int smem_bytes, int n_units)
+int grid_for(const void *kernel, int smem_bytes, int n_units)
 {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, kThreads, smem_bytes);
-    per_sm = std::max(per_sm, 1);
+    int per_sm = std::max(blocks_per_sm(kernel, smem_bytes), 1);
     return std::max(1, std::min(n_units, per_sm * g_num_sms));
 }
 
@@ -329,11 +384,9 @@ sqa_status launch_sweeps(sqa_handle *h, int t0, int t1, int u0, int nu, cudaStre
 {
     h->job.t0 = t0;
     h->job.t1 = t1;
-    SQA_CUDA(cudaMemcpyAsync(h->d_job, &h->job, sizeof(JobDev), cudaMemcpyHostToDevice, s));
     SQA_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
-    const int grid = grid_for(h->job.smem_bytes, nu);
-    sweep_kernel<<<grid, kThreads, h->job.smem_bytes, s>>>(h->d_job, h->d_units + u0, nu, h->d_counter);
-    SQA_CUDA(cudaGetLastError());
+    const int grid = grid_for(one_kernel(h->job), h->job.smem_bytes, nu);
+    SQA_CUDA(launch_sweep_one(h->job, h->d_units + u0, nu, h->d_counter, grid, s));
     return SQA_OK;
 }
 
@@ -467,6 +520,43 @@ sqa_status sqa_get_info(const sqa_handle *h, sqa_info *o)
     return SQA_OK;
 }
 
+sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table)
+{
+    if (!h || words_per_unit < 0 || use_table < -1 || use_table > 1) return set_error("tune arguments"), SQA_ERR_INVALID;
+    if (use_table == 0 && h->window_limit_exceeded) return set_error("window mode cannot hold this problem"), SQA_ERR_UNSUPPORTED;
+    const int old_wc = h->force_wc, old_mode = h->force_mode;
+    h->force_wc = words_per_unit;
+    h->force_mode = use_table;
+    const JobDev keep = h->job;
+    const std::vector<Unit> keep_units = h->units;
+    sqa_status st = plan_units(h);
+    if (st != SQA_OK) {
+        h->force_wc = old_wc;
+        h->force_mode = old_mode;
+        h->job = keep;
+        h->units = keep_units;
+        return st;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "sqa_tune");
+    SQA_CUDA(cudaFree(h->d_units));
+    for (auto &p : h->allocs)
+        if (p == (void *)h->d_units) p = nullptr;
+    h->d_units = nullptr;
+    if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) return st;
+    h->n_units = (int)h->units.size();
+    return SQA_OK;
+}
+
+sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t *use_table, int32_t *smem_bytes)
+{
+    if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
+    if (words_per_unit) *words_per_unit = h->job.wc;
+    if (use_table) *use_table = h->job.use_lut;
+    if (smem_bytes) *smem_bytes = h->job.smem_bytes;
+    return SQA_OK;
+}
+
 sqa_status sqa_run_sweeps(sqa_handle *h, int32_t t0, int32_t t1, void *stream)
 {
     if (!h || t0 < 0 || t1 < t0 || t1 > h->S) return set_error("sweep range"), SQA_ERR_INVALID;
@@ -558,7 +648,7 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
     SQA_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, s));
     SQA_CUDA(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s));
     SQA_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
-    const int grid = grid_for(smem, (int)units.size());
+    const int grid = grid_for((const void *)sweep_kernel, smem, (int)units.size());
     sweep_kernel<<<grid, kThreads, smem, s>>>(d_jobs, d_units, (int)units.size(), d_counter);
     SQA_CUDA(cudaGetLastError());
     SQA_CUDA(cudaFreeAsync(d_jobs, s));

@@ -176,10 +176,13 @@ void build_sites(const Plan &pl, const int32_t *J, int penalty, int K, int smax_
                  std::vector<SiteRec> &out)
 {
     out.assign(pl.n, SiteRec{});
+    int lut = 0;
     for (int i = 0; i < pl.n; i++) {
         SiteRec &r = out[i];
         r.nterm = (int16_t)pl.site_terms[i].size();
         r.canon = pl.canon[i];
+        r.lut_off = lut;
+        lut += 1 << (r.nterm + 2);
         int S = 0;
         for (int q = 0; q < kMaxTerms; q++) {
             TermRec &tr = r.t[q];

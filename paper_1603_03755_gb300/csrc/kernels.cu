@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "layout.cuh"
 #include "philox.cuh"
 #include "sqa_internal.h"
 
@@ -36,11 +37,6 @@ __device__ __forceinline__ uint32_t valid_bits(int R, int gw)
 }
 
 __device__ __forceinline__ uint32_t bytes4(uint32_t v, int j) { return (v >> j) & 0x01010101u; }
-
-__device__ __forceinline__ U4 pick4(const U4 &a, const U4 &b, const U4 &c, const U4 &d, int r)
-{
-    return r == 0 ? a : (r == 1 ? b : (r == 2 ? c : d));
-}
 
 // ---------------------------------------------------------------------------
 // Initial spins: bit (r % 32) of word (r/32) % 4 of the INIT stream at
@@ -69,7 +65,9 @@ __global__ void init_kernel(JobDev J, const int *canon)
 // ---------------------------------------------------------------------------
 struct Smem {
     uint32_t *S;      // [Z][zstride]
-    uint32_t *T;      // SQA: one row; PT: P rows
+    uint32_t *T;      // full thresholds: SQA one row, PT P rows
+    int32_t *Tq;      // PT: -(T high half << 15), P rows
+    int32_t *lut;     // SQA: per-site tables, -(T high half << 15) by code
     SiteRec *sites;   // [n]
     int32_t *E;       // PT: [P][wc*32]
     uint32_t *M;      // PT: swap masks [P/2+1][wc]
@@ -77,26 +75,25 @@ struct Smem {
 
 __device__ __forceinline__ Smem carve(const JobDev &J, unsigned char *base)
 {
+    const SmemOffsets o = smem_layout(J, J.wc, J.zstride);
     Smem m;
-    size_t off = 0;
-    m.S = (uint32_t *)(base + off);
-    off += (size_t)J.Z * J.zstride * 4;
-    m.T = (uint32_t *)(base + off);
-    off += (size_t)(J.kind == SQA_KIND_SQA ? J.nrow : J.Z * J.nrow) * 4;
-    off = (off + 15) & ~(size_t)15;
-    m.sites = (SiteRec *)(base + off);
-    off += (size_t)J.n * sizeof(SiteRec);
-    m.E = (int32_t *)(base + off);
-    m.M = nullptr;
-    if (J.kind == SQA_KIND_PT) {
-        off += (size_t)J.Z * J.wc * 32 * 4;
-        m.M = (uint32_t *)(base + off);
-    }
+    m.S = (uint32_t *)(base + o.S);
+    m.T = (uint32_t *)(base + o.T);
+    m.Tq = (int32_t *)(base + o.Tq);
+    m.lut = (int32_t *)(base + o.lut);
+    m.sites = (SiteRec *)(base + o.sites);
+    m.E = (int32_t *)(base + o.E);
+    m.M = (uint32_t *)(base + o.M);
     return m;
 }
 
-// Term planes of one item: pl[k] has bit b set when term k's value is
-// negative for replica b; kw[k] is K * |w_k|.
+// Negated high half of a threshold, scaled to 31 bits: for a 31-bit value x
+// whose top 16 bits are a uniform's high half h, x + q is negative iff
+// h < T >> 16, and lies in [0, 2^15) iff h == T >> 16 (a tie).
+__device__ __forceinline__ int32_t neg_high(uint32_t T) { return -(int32_t)((T >> 1) & 0x7FFF8000u); }
+
+// Term planes of one item: bit b of pl[k] is set when term k's value is
+// negative for replica b (it turns positive on a flip).  kw[k] is K*|w_k|.
 __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *row, int wc, int w,
                                             uint32_t s, uint32_t (&pl)[kMaxTerms],
                                             uint32_t (&kw)[kMaxTerms])
@@ -112,90 +109,192 @@ __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *r
             if (tr.p[1] >= 0) p ^= row[tr.p[1] * wc + w];
             if (tr.p[2] >= 0) p ^= row[tr.p[2] * wc + w];
             const int wv = tr.w;
-            // value w * prod(sigma) is negative iff (product is -1) xor (w < 0)
-            const uint32_t neg = (uint32_t)(wv >> 31);
-            pl[k] = p ^ neg;
+            // w * prod(sigma) is negative iff (product is -1) xor (w < 0)
+            pl[k] = p ^ (uint32_t)(wv >> 31);
             kw[k] = (uint32_t)(wv < 0 ? -wv : wv);
         }
     }
 }
 
-// Byte-wise window offsets of replicas (j, j+8, j+16, j+24).  A term whose
-// value is negative turns positive on a flip: it raises delta by 2|w|, which
-// is K*|w|/... in row units; see build_sites.
-template <int KIND>
+// PT threshold index bytes of replicas (j, j+8, j+16, j+24): sum of K*|w| over
+// the terms that turn positive, added byte-wise.
 __device__ __forceinline__ uint32_t window4(const uint32_t (&pl)[kMaxTerms],
-                                            const uint32_t (&kw)[kMaxTerms], uint32_t d1,
-                                            uint32_t d2, int j)
+                                            const uint32_t (&kw)[kMaxTerms], int j)
 {
-    uint32_t a = KIND == SQA_KIND_SQA ? 0x02020202u : 0u;
+    uint32_t a = 0u;
 #pragma unroll
     for (int k = 0; k < kMaxTerms; k++) a += kw[k] * bytes4(pl[k], j);
-    if (KIND == SQA_KIND_SQA) a -= bytes4(d1, j) + bytes4(d2, j);
     return a;
 }
 
+// Bit-matrix transpose of four 8x8 blocks held in eight words: afterwards byte
+// b of P[j] holds bit (8b + j) of every input word, input word i at bit i.
+__device__ __forceinline__ void transpose8(uint32_t (&P)[8])
+{
+#define SQA_SWAP(a, b, d, m)                                   \
+    {                                                          \
+        const uint32_t t_ = ((P[a] >> (d)) ^ P[b]) & (m);      \
+        P[b] ^= t_;                                            \
+        P[a] ^= t_ << (d);                                     \
+    }
+    SQA_SWAP(0, 4, 4, 0x0F0F0F0Fu) SQA_SWAP(1, 5, 4, 0x0F0F0F0Fu)
+    SQA_SWAP(2, 6, 4, 0x0F0F0F0Fu) SQA_SWAP(3, 7, 4, 0x0F0F0F0Fu)
+    SQA_SWAP(0, 2, 2, 0x33333333u) SQA_SWAP(1, 3, 2, 0x33333333u)
+    SQA_SWAP(4, 6, 2, 0x33333333u) SQA_SWAP(5, 7, 2, 0x33333333u)
+    SQA_SWAP(0, 1, 1, 0x55555555u) SQA_SWAP(2, 3, 1, 0x55555555u)
+    SQA_SWAP(4, 5, 1, 0x55555555u) SQA_SWAP(6, 7, 1, 0x55555555u)
+#undef SQA_SWAP
+}
+
+// Division by a runtime divisor d >= 1 for numerators x < 2^31:
+// floor(x/d) = umulhi(x, m) >> sh with m = ceil(2^(31+l)/d), l = ceil(log2 d),
+// sh = l - 1; d = 1 is m = 0 (quotient x).
+struct FastDiv {
+    uint32_t d, m, sh;
+};
+
+__device__ __forceinline__ FastDiv make_div(uint32_t d)
+{
+    FastDiv f;
+    f.d = d;
+    if (d <= 1) {
+        f.m = 0;
+        f.sh = 0;
+        return f;
+    }
+    const uint32_t l = 32u - __clz(d - 1u);  // ceil(log2 d)
+    const unsigned long long num = 1ull << (31 + l);
+    f.m = (uint32_t)((num + d - 1) / d);
+    f.sh = l - 1u;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f)
+{
+    return f.m == 0 ? x : (__umulhi(x, f.m) >> f.sh);
+}
+
+// The keys of the two sweep streams.
+struct Keys {
+    uint32_t k0, khi, klo;
+};
+
+// Full threshold index of replica (r, j) from its code (SQA: bit 0, 1 = the
+// two temporal disagreements, bit 2+k = term k negative) or PT index byte.
 template <int KIND>
-__device__ __forceinline__ void sweep_item(const JobDev &J, const Smem &sm, int inst, int w0, int wc,
-                                           int t, int si, int z, int w)
+__device__ __forceinline__ int full_index(const SiteRec &sr, uint32_t code)
+{
+    if (KIND == SQA_KIND_SQA) {
+        int U = 2 - (int)(code & 1u) - (int)((code >> 1) & 1u);
+#pragma unroll
+        for (int k = 0; k < kMaxTerms; k++)
+            if (k < sr.nterm && ((code >> (k + 2)) & 1u)) {
+                const int wv = sr.t[k].w;
+                U += wv < 0 ? -wv : wv;
+            }
+        return sr.base + U;
+    }
+    return sr.base + (int)code;
+}
+
+// One item: the word of 32 replicas of site si at slice/slot z.  Byte r of
+// code[j] selects replica j + 8r's threshold: a per-site table entry (SQA,
+// table mode) or an index in the site's window of the threshold row.
+template <int KIND, bool LUT>
+__device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const Smem &sm, int inst, int w0,
+                                           int wc, int t, int si, int z, int w)
 {
     const SiteRec &sr = sm.sites[si];
     uint32_t *row = sm.S + (size_t)z * J.zstride;
     const uint32_t s = row[si * wc + w];
-    uint32_t d1 = 0u, d2 = 0u;
     const int Z = J.Z;
-    if (KIND == SQA_KIND_SQA) {
-        const int zu = z == 0 ? Z - 1 : z - 1;
-        const int zd = z == Z - 1 ? 0 : z + 1;
-        // a temporal neighbour that disagrees lowers m by 2: m = 2 - 2*tc
-        d1 = s ^ sm.S[(size_t)zu * J.zstride + si * wc + w];
-        d2 = s ^ sm.S[(size_t)zd * J.zstride + si * wc + w];
+    uint32_t code[8];
+    {
+        uint32_t pl[kMaxTerms], kw[kMaxTerms];
+        term_planes(sr, row, wc, w, s, pl, kw);
+        uint32_t d1 = 0u, d2 = 0u;
+        if (KIND == SQA_KIND_SQA) {
+            const int zu = z == 0 ? Z - 1 : z - 1;
+            const int zd = z == Z - 1 ? 0 : z + 1;
+            // temporal disagreements: m = sigma (sigma_up + sigma_dn) = 2 - 2 (d1 + d2)
+            d1 = s ^ sm.S[(size_t)zu * J.zstride + si * wc + w];
+            d2 = s ^ sm.S[(size_t)zd * J.zstride + si * wc + w];
+        }
+        if (KIND == SQA_KIND_SQA && LUT) {
+            code[0] = d1;
+            code[1] = d2;
+#pragma unroll
+            for (int k = 0; k < kMaxTerms; k++) code[k + 2] = pl[k];
+            transpose8(code);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                uint32_t a = window4(pl, kw, j);
+                if (KIND == SQA_KIND_SQA) a += 0x02020202u - bytes4(d1, j) - bytes4(d2, j);
+                code[j] = a;
+            }
+        }
     }
-    uint32_t pl[kMaxTerms], kw[kMaxTerms];
-    term_planes(sr, row, wc, w, s, pl, kw);
-
+    const int32_t *Q = (KIND == SQA_KIND_SQA && LUT) ? sm.lut + sr.lut_off
+                       : (KIND == SQA_KIND_SQA ? sm.Tq + sr.base : sm.Tq + (size_t)z * J.nrow + sr.base);
+    const uint32_t *Tfull = KIND == SQA_KIND_SQA ? sm.T : sm.T + (size_t)z * J.nrow;
     const int gw = w0 + w;
     const uint32_t slot = (uint32_t)(sr.canon * Z + z);
     const uint32_t g0 = (uint32_t)gw * 4u;
-    const U4 A0 = philox((uint32_t)t, slot, g0 + 0u, (uint32_t)inst, J.seed_lo, J.key_hi);
-    const U4 A1 = philox((uint32_t)t, slot, g0 + 1u, (uint32_t)inst, J.seed_lo, J.key_hi);
-    const U4 A2 = philox((uint32_t)t, slot, g0 + 2u, (uint32_t)inst, J.seed_lo, J.key_hi);
-    const U4 A3 = philox((uint32_t)t, slot, g0 + 3u, (uint32_t)inst, J.seed_lo, J.key_hi);
-    const uint32_t *Trow = KIND == SQA_KIND_SQA ? sm.T : sm.T + (size_t)z * J.nrow;
-    const int base = sr.base;
-
-    uint32_t acc = 0u, tie = 0u;
+    uint32_t acc = 0u;
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-        const uint32_t a = window4<KIND>(pl, kw, d1, d2, j);
+    for (int r = 3; r >= 0; r--) {
+        const U4 Ar = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.khi);
+        uint32_t hi = 0u;
+        bool tie = false;
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
-            const uint32_t T = Trow[base + ((a >> (8 * r)) & 0xFFu)];
-            const U4 &Ar = r == 0 ? A0 : (r == 1 ? A1 : (r == 2 ? A2 : A3));
+        for (int j = 7; j >= 0; j--) {
+            const int32_t q = Q[__byte_perm(code[j], 0u, 0x4440u + (uint32_t)r)];
             const uint32_t aw = word_of(Ar, j >> 1);
-            const uint32_t uh = (j & 1) ? (aw & 0xFFFF0000u) : (aw << 16);
-            const uint32_t bit = 1u << (j + 8 * r);
-            if ((uh | 0xFFFFu) < T) acc |= bit;           // high half decides: accept
-            if ((uh ^ T) < 0x10000u) tie |= bit;          // high halves equal: undecided
+            // the replica's 16 high uniform bits at bits 15..30 of x
+            const uint32_t x = (j & 1) ? (aw >> 1) : ((aw & 0xFFFFu) << 15);
+            const uint32_t d = x + (uint32_t)q;
+            hi = __funnelshift_l(d, hi, 1);  // append the sign bit: accepted
+            tie |= d < 0x8000u;
         }
-    }
-    while (tie) {
-        const int b = __ffs(tie) - 1;
-        tie &= tie - 1u;
-        const int j = b & 7, r = b >> 3;
-        const U4 Br = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, J.seed_lo, J.key_lo);
-        const U4 Ar = pick4(A0, A1, A2, A3, r);
-        const uint32_t sh = 16u * (uint32_t)(j & 1);
-        uint32_t u = (((word_of(Ar, j >> 1) >> sh) & 0xFFFFu) << 16) | ((word_of(Br, j >> 1) >> sh) & 0xFFFFu);
-        u = u < 0xFFFFFFFEu ? u : 0xFFFFFFFEu;
-        const uint32_t a = window4<KIND>(pl, kw, d1, d2, j);
-        const uint32_t T = Trow[base + ((a >> (8 * r)) & 0xFFu)];
-        if (u < T)
-            acc |= 1u << b;
-        else
-            acc &= ~(1u << b);
+        if (tie) {
+            // high halves equal (probability 2^-16): draw the low half and
+            // compare the whole uniform with the whole threshold
+            const U4 Br = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.klo);
+#pragma unroll
+            for (int j = 7; j >= 0; j--) {
+                const uint32_t c = __byte_perm(code[j], 0u, 0x4440u + (uint32_t)r);
+                const uint32_t aw = word_of(Ar, j >> 1);
+                const uint32_t x = (j & 1) ? (aw >> 1) : ((aw & 0xFFFFu) << 15);
+                const uint32_t d = x + (uint32_t)Q[c];
+                if (d < 0x8000u) {
+                    const uint32_t sh = 16u * (uint32_t)(j & 1);
+                    uint32_t u = ((aw >> sh) & 0xFFFFu) << 16 | ((word_of(Br, j >> 1) >> sh) & 0xFFFFu);
+                    u = u < 0xFFFFFFFEu ? u : 0xFFFFFFFEu;
+                    const uint32_t T = Tfull[LUT ? full_index<KIND>(sr, c) : sr.base + (int)c];
+                    if (u < T)
+                        hi |= 1u << j;
+                    else
+                        hi &= ~(1u << j);
+                }
+            }
+        }
+        acc = (acc << 8) | hi;
     }
     row[si * wc + w] = s ^ (acc & valid_bits(J.R, gw));
+}
+
+// SQA: per-site tables for sweep t from the staged threshold row: entry c is
+// the negated high half of T[base + 2 + sum of K|w_k| over set term bits
+// - the two temporal bits].
+__device__ void build_luts(const JobDev &J, const Smem &sm)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int si = warp; si < J.n; si += nw) {
+        const SiteRec &sr = sm.sites[si];
+        const int ne = 1 << (sr.nterm + 2);
+        for (int c = lane; c < ne; c += 32) sm.lut[sr.lut_off + c] = neg_high(sm.T[full_index<SQA_KIND_SQA>(sr, (uint32_t)c)]);
+    }
 }
 
 // PT: energies of every (slot, replica) of the unit, then the swap event.
@@ -221,7 +320,7 @@ __device__ void pt_swap(const JobDev &J, const Smem &sm, int inst, int w0, int w
     }
     __syncthreads();
     const int p0 = e & 1;
-    const int npairs = p0 + 1 < P ? (P - 1 - p0 + 1) / 2 : 0;
+    const int npairs = p0 + 1 < P ? (P - p0) / 2 : 0;
     for (int it = threadIdx.x; it < npairs * wc * 32; it += nthr) {
         const int b = it & 31, r = it >> 5, w = r % wc, k = r / wc;
         const int p = p0 + 2 * k;
@@ -250,11 +349,12 @@ __device__ void pt_swap(const JobDev &J, const Smem &sm, int inst, int w0, int w
     __syncthreads();
 }
 
-template <int KIND>
+template <int KIND, bool LUT>
 __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 {
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int Z = J.Z, n = J.n, wc = u.wc, inst = u.inst, w0 = u.w0;
+    const Keys K{J.seed_lo, J.key_hi, J.key_lo};
     // stage state and site records
     for (int i = tid; i < Z * n * wc; i += nthr) {
         const int w = i % wc, r = i / wc, si = r % n, z = r / n;
@@ -266,21 +366,36 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
         for (int i = tid; i < n * (int)(sizeof(SiteRec) / 4); i += nthr) dst[i] = src[i];
     }
     if (KIND == SQA_KIND_PT)
-        for (int i = tid; i < Z * J.nrow; i += nthr) sm.T[i] = J.T[i];
+        for (int i = tid; i < Z * J.nrow; i += nthr) {
+            const uint32_t T = J.T[i];
+            sm.T[i] = T;
+            sm.Tq[i] = neg_high(T);
+        }
     __syncthreads();
+    const FastDiv div_w = make_div((uint32_t)wc);
+    const FastDiv div_z = make_div((uint32_t)(KIND == SQA_KIND_SQA ? (Z >> 1) : Z));
 
     for (int t = J.t0; t < J.t1; t++) {
         if (KIND == SQA_KIND_SQA) {
-            for (int i = tid; i < J.nrow; i += nthr) sm.T[i] = __ldg(J.T + (size_t)t * J.nrow + i);
+            for (int i = tid; i < J.nrow; i += nthr) {
+                const uint32_t T = __ldg(J.T + (size_t)t * J.nrow + i);
+                sm.T[i] = T;
+                if (!LUT) sm.Tq[i] = neg_high(T);
+            }
             __syncthreads();
+            if (LUT) {
+                build_luts(J, sm);
+                __syncthreads();
+            }
             const int half = Z >> 1;
             for (int cls = 0; cls < 2 * J.ncol; cls++) {
                 const int chi = cls >> 1, par = cls & 1;
                 const int c0 = J.col_ptr[chi];
                 const int nitems = (J.col_ptr[chi + 1] - c0) * half * wc;
                 for (int it = tid; it < nitems; it += nthr) {
-                    const int w = it % wc, r = it / wc, zh = r % half, si = c0 + r / half;
-                    sweep_item<SQA_KIND_SQA>(J, sm, inst, w0, wc, t, si, 2 * zh + par, w);
+                    const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
+                    const int q = (int)fdiv((uint32_t)r, div_z), zh = r - q * half;
+                    sweep_item<SQA_KIND_SQA, LUT>(J, K, sm, inst, w0, wc, t, c0 + q, 2 * zh + par, w);
                 }
                 __syncthreads();
             }
@@ -289,8 +404,9 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 const int c0 = J.col_ptr[chi];
                 const int nitems = (J.col_ptr[chi + 1] - c0) * Z * wc;
                 for (int it = tid; it < nitems; it += nthr) {
-                    const int w = it % wc, r = it / wc, p = r % Z, si = c0 + r / Z;
-                    sweep_item<SQA_KIND_PT>(J, sm, inst, w0, wc, t, si, p, w);
+                    const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
+                    const int q = (int)fdiv((uint32_t)r, div_z), p = r - q * Z;
+                    sweep_item<SQA_KIND_PT, false>(J, K, sm, inst, w0, wc, t, c0 + q, p, w);
                 }
                 __syncthreads();
             }
@@ -303,11 +419,16 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
     }
 }
 
-__global__ void __launch_bounds__(256) sweep_kernel(const JobDev *jobs, const Unit *units, int n_units,
-                                                    int *counter)
+// One job: the descriptor is a kernel parameter, so its fields (the Philox
+// keys among them) are uniform across the grid.  One instantiation per path
+// (0 PT, 1 SQA windows, 2 SQA tables) so each gets its own registers.
+template <int MODE>
+__global__ void __launch_bounds__(256, 3) sweep_kernel_one(const __grid_constant__ JobDev J, const Unit *units,
+                                                           int n_units, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_unit;
+    const Smem sm = carve(J, smem_raw);
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
         __syncthreads();
@@ -315,12 +436,69 @@ __global__ void __launch_bounds__(256) sweep_kernel(const JobDev *jobs, const Un
         __syncthreads();
         if (ui >= n_units) break;
         const Unit u = units[ui];
-        const JobDev &J = jobs[u.job];
-        const Smem sm = carve(J, smem_raw);
-        if (J.kind == SQA_KIND_SQA)
-            run_unit<SQA_KIND_SQA>(J, sm, u);
+        if (MODE == 0)
+            run_unit<SQA_KIND_PT, false>(J, sm, u);
+        else if (MODE == 2)
+            run_unit<SQA_KIND_SQA, true>(J, sm, u);
         else
-            run_unit<SQA_KIND_PT>(J, sm, u);
+            run_unit<SQA_KIND_SQA, false>(J, sm, u);
+        __syncthreads();
+    }
+}
+
+// Host side of the single-job kernel: its entry for a job's path, and the
+// launch.
+static int one_mode(const JobDev &J) { return J.kind == SQA_KIND_PT ? 0 : (J.use_lut ? 2 : 1); }
+
+const void *sweep_one_entry(const JobDev &J)
+{
+    switch (one_mode(J)) {
+    case 0: return (const void *)sweep_kernel_one<0>;
+    case 1: return (const void *)sweep_kernel_one<1>;
+    default: return (const void *)sweep_kernel_one<2>;
+    }
+}
+
+const void *sweep_one_entry_mode(int mode)
+{
+    return mode == 0 ? (const void *)sweep_kernel_one<0>
+                     : (mode == 1 ? (const void *)sweep_kernel_one<1> : (const void *)sweep_kernel_one<2>);
+}
+
+cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, int *counter, int grid,
+                             cudaStream_t s)
+{
+    switch (one_mode(J)) {
+    case 0: sweep_kernel_one<0><<<grid, 256, J.smem_bytes, s>>>(J, units, n_units, counter); break;
+    case 1: sweep_kernel_one<1><<<grid, 256, J.smem_bytes, s>>>(J, units, n_units, counter); break;
+    default: sweep_kernel_one<2><<<grid, 256, J.smem_bytes, s>>>(J, units, n_units, counter); break;
+    }
+    return cudaGetLastError();
+}
+
+// Several jobs of any shapes: each unit names its job; the block copies that
+// job's descriptor into shared memory.
+__global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const Unit *units, int n_units,
+                                                       int *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_unit;
+    __shared__ JobDev s_job;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int ui = s_unit;
+        if (ui < n_units && threadIdx.x == 0) s_job = jobs[units[ui].job];
+        __syncthreads();
+        if (ui >= n_units) break;
+        const Unit u = units[ui];
+        const Smem sm = carve(s_job, smem_raw);
+        if (s_job.kind == SQA_KIND_PT)
+            run_unit<SQA_KIND_PT, false>(s_job, sm, u);
+        else if (s_job.use_lut)
+            run_unit<SQA_KIND_SQA, true>(s_job, sm, u);
+        else
+            run_unit<SQA_KIND_SQA, false>(s_job, sm, u);
         __syncthreads();
     }
 }

@@ -1,0 +1,58 @@
+// Shared-memory layout of one unit of the sweep kernel, computed the same way
+// on the host (launch sizing) and on the device (carving).
+#pragma once
+#include <stddef.h>
+
+#include "sqa_internal.h"
+
+#if defined(__CUDACC__)
+#define SQA_LHD __host__ __device__ __forceinline__
+#else
+#define SQA_LHD inline
+#endif
+
+namespace sqa {
+
+struct SmemOffsets {
+    size_t S;      // state [Z][zstride] words
+    size_t T;      // full thresholds: SQA one row, PT P rows
+    size_t Tq;     // negated high halves of the thresholds: PT P rows, SQA window mode one row
+    size_t lut;    // SQA: per-site tables of negated high halves
+    size_t sites;  // SiteRec [n]
+    size_t E;      // PT: energies [P][wc*32]
+    size_t M;      // PT: swap masks [P/2+1][wc]
+    size_t total;
+};
+
+SQA_LHD size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
+{
+    SmemOffsets o;
+    size_t off = 0;
+    o.S = off;
+    off += (size_t)J.Z * zstride * 4;
+    o.T = off;
+    off += (size_t)(J.kind == SQA_KIND_SQA ? J.nrow : J.Z * J.nrow) * 4;
+    o.Tq = off;
+    if (J.kind == SQA_KIND_PT)
+        off += (size_t)J.Z * J.nrow * 4;
+    else if (!J.use_lut)
+        off += (size_t)J.nrow * 4;
+    o.lut = off;
+    if (J.kind == SQA_KIND_SQA && J.use_lut) off += (size_t)J.lut_entries * 4;
+    off = align16(off);
+    o.sites = off;
+    off += (size_t)J.n * sizeof(SiteRec);
+    o.E = off;
+    o.M = off;
+    if (J.kind == SQA_KIND_PT) {
+        off += (size_t)J.Z * wc * 32 * 4;
+        o.M = off;
+        off += (size_t)(J.Z / 2 + 1) * wc * 4;
+    }
+    o.total = align16(off);
+    return o;
+}
+
+}  // namespace sqa

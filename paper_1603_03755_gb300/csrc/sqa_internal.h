@@ -23,11 +23,12 @@ struct TermRec {
     int16_t w;     // K * |weight|, negative when the weight is negative
 };
 
-// Everything a sweep needs about one site (56 bytes).
+// Everything a sweep needs about one site (60 bytes).
 struct SiteRec {
     int16_t nterm;
-    int16_t base;   // start of the site's window in a threshold row
-    int32_t canon;  // canonical site id: random-number counters, readout
+    int16_t base;     // start of the site's window in a threshold row
+    int32_t canon;    // canonical site id: random-number counters, readout
+    int32_t lut_off;  // SQA: offset of the site's 2^(nterm+2)-entry table
     TermRec t[kMaxTerms];
 };
 
@@ -67,6 +68,8 @@ struct JobDev {
     int wc;          // words per unit
     int zstride;     // shared-memory words per z row
     int smem_bytes;  // shared memory of one unit
+    int lut_entries; // SQA: sum over sites of 2^(nterm+2)
+    int use_lut;     // SQA: 1 = per-site code tables, 0 = byte-wise index windows
     int pad_;
 };
 

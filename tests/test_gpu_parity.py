@@ -229,3 +229,24 @@ def test_full_size_me_k8_batch_sampled():
         assert np.array_equal(got[:, :, r0:r1], q.s[:, :, r0:r1])
         for z in (0, 31, 63):
             assert np.array_equal(E[inst, z, r0:r1], pb.energies(got[z])[r0:r1])
+
+
+@pytest.mark.parametrize("emb,use_table,wc", [("lhz", 0, 0), ("lhz", 1, 0), ("me", 0, 1), ("me", 1, 2),
+                                              ("lhz", -1, 3), ("me", 1, 5)])
+def test_launch_shapes_give_the_oracle_bits(emb, use_table, wc):
+    """Table or window threshold lookup, any words per block: same bits."""
+    N, L, R, S = 8, 8, 150, 20                      # 5 words, ragged last word
+    pen = 6 if emb == "me" else 9
+    J = W.random_instances(N, 2, 77)
+    h = pkg.Handle(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=77, L=L, beta=3.0)
+    h.tune(wc, use_table)
+    got = h.launch()
+    if use_table >= 0:
+        assert got["use_table"] == use_table
+    if wc:
+        assert got["words_per_unit"] == wc
+    h.run(stream=0)
+    st = gpu_state(h)
+    for i in range(2):
+        pb, q = oracle_sqa(emb, N, J[i], pen, L, R, 3.0, S, 77, i)
+        assert np.array_equal(st[i], q.s)
