@@ -169,6 +169,22 @@ sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *lo
  * e_out host [I].  N <= 40.  Synchronous. */
 sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, int64_t *e_out);
 
+/* Exhaustive ground-state energies for callers that cannot allocate device
+ * memory (e.g. a serving process that reserved its whole device budget up
+ * front, or code under a memory manager that forbids ad-hoc cudaMalloc).  The
+ * paper has no counterpart: this is a service entry point of the library.
+ * Same search and result as sqa_ground_energy, but J_dev ([I][N(N-1)/2]
+ * int32) and e_dev ([I] int64) are caller-owned device buffers, the call is
+ * asynchronous on stream, and nothing is allocated: the per-instance running
+ * minima live in a fixed device array of 4096 entries (32 KiB held on every
+ * device that loads the library, until exit).  I > 4096 or N outside 2..40
+ * -> SQA_ERR_INVALID.  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  All calls share the array and reset it at the start,
+ * so calls that overlap on the GPU race with each other. */
+sqa_status sqa_ground_energy_noalloc(int32_t N, int32_t n_instances, const int32_t *J_dev,
+                                     int64_t *e_dev, void *stream);
+
 /* ---- host-only views of the library's planning (no device needed) ---- */
 
 /* The physical problem the library builds for one instance (Sec. II A/B):

@@ -66,6 +66,7 @@ _SIGS = {
     "sqa_decode": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_int32, C.c_void_p]),
     "sqa_ground_energy": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "sqa_ground_energy_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sqa_plan_terms": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sqa_plan_tables": (C.c_int, [C.POINTER(_Desc), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -261,6 +262,14 @@ def int_peak(kind: str) -> float:
     v = C.c_double()
     _check(lib().sqa_int_peak(INT_PEAK_KINDS.index(kind), C.byref(v)), "sqa_int_peak")
     return v.value
+
+
+def ground_energy_noalloc(N: int, J_dev, e_dev, stream=None):
+    """Allocation-free ground-state search: J_dev [I, N(N-1)/2] int32 and
+    e_dev [I] int64 are caller-owned CUDA tensors; asynchronous on stream."""
+    assert J_dev.is_cuda and e_dev.is_cuda and J_dev.is_contiguous() and e_dev.is_contiguous()
+    _check(lib().sqa_ground_energy_noalloc(N, e_dev.shape[0], J_dev.data_ptr(), e_dev.data_ptr(),
+                                           _stream_ptr(stream)), "sqa_ground_energy_noalloc")
 
 
 def unpack_words(words, R: int) -> np.ndarray:
