@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--per-instance-sample", type=int, default=8,
                     help="instances timed on the one-launch-per-instance path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the ragged-batch and PT workloads")
+    ap.add_argument("--pt-sweeps", type=int, default=100_000)
+    ap.add_argument("--ragged-sweeps", type=int, default=10_000)
     return ap.parse_args()
 
 
@@ -158,6 +161,59 @@ def cpu_oracle_sample(cfg, seconds_budget=15.0, first_instance=0):
     attempts = n_used * L * R * t
     desc = f"instance {first_instance}, replicas 0-31, sweeps 0-{t - 1} of the {S}-sweep anneal, 1 thread"
     return attempts / dt, desc, attempts
+
+
+def timed(stream, fn):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    stream.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def extra_workloads(pkg, stream, args):
+    """The ragged LHZ/ME mix in one persistent launch, and PT on ME K_32 and
+    LHZ K_24 (32 temperatures, swap every sweep).  Each timed once after a
+    short warm-up run of the same shapes."""
+    sp = stream.cuda_stream
+    out = {}
+    jobs = W.ragged_mix_config(512, R=128, sweeps=args.ragged_sweeps)
+
+    def make(js, sweeps):
+        return [pkg.Handle(embedding=j["embedding"], N=j["N"], J=j["J"], penalty=j["penalty"], sweeps=sweeps,
+                           R=j["R"], seed=j["seed"], L=j["L"], beta=j["beta"]) for j in js]
+
+    warm = make(jobs, 20)
+    pkg.batch_run(warm, stream=sp)
+    stream.synchronize()
+    for h in warm:
+        h.close()
+    hs = make(jobs, args.ragged_sweeps)
+    att = sum(h.info["attempts_per_sweep"] for h in hs) * args.ragged_sweeps
+    t = timed(stream, lambda: pkg.batch_run(hs, stream=sp))
+    out["ragged_mix"] = {"workload": f"ragged LHZ N 8-16 / ME N 8-16, L 32/64, 512 instances x 128 replicas, "
+                                     f"{args.ragged_sweeps} sweeps, one persistent launch",
+                         "value": att / t, "unit": UNIT, "seconds": t}
+    for h in hs:
+        h.close()
+    for emb in ("me", "lhz"):
+        c = W.pt_config(emb, sweeps=args.pt_sweeps)
+        kw = dict(embedding=emb, N=c["N"], J=c["J"], penalty=c["penalty"], R=c["R"], seed=c["seed"], kind="pt",
+                  betas=c["betas"], swap_every=c["swap_every"])
+        w = pkg.Handle(sweeps=50, **kw)
+        w.run(stream=sp)
+        stream.synchronize()
+        w.close()
+        h = pkg.Handle(sweeps=args.pt_sweeps, **kw)
+        att = h.info["attempts_per_sweep"] * args.pt_sweeps
+        t = timed(stream, lambda: h.run(stream=sp))
+        out[f"pt_{emb}"] = {"workload": c["name"] + f", 32 temperatures, {args.pt_sweeps} sweeps, swap every sweep",
+                            "value": att / t, "unit": UNIT, "seconds": t, "launch": h.launch()}
+        h.close()
+    return out
 
 
 def run_reference(args, cfg, world, rank, dist):
@@ -319,6 +375,7 @@ def main():
     intpeak = {k: round(pkg.int_peak(k), 2) for k in pkg.INT_PEAK_KINDS}
     t_sweep = statistics.mean(sweep_times)
     achieved_gops = attempts * OPS_PER_ATTEMPT / t_sweep / 1e9
+    extra = None if args.no_extra else extra_workloads(pkg, stream, args)
     cpu = None
     if not args.no_cpu_baseline:
         rate, desc, _ = cpu_oracle_sample(cfg)
@@ -344,6 +401,8 @@ def main():
                               "same_bits_as_batched": bool(same),
                               "batched_over_per_instance": value / world / per_inst_rate},
         "peaks_source": src,
+        "other_workloads": extra,
+        "launch": h.launch(),
     }
     print(json.dumps(out))
     barrier(dist)

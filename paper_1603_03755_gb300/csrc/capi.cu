@@ -98,6 +98,7 @@ struct sqa_handle {
     SiteRec *d_sites = nullptr;
     uint32_t *d_T = nullptr;
     ETerm *d_eterms = nullptr;
+    EClass *d_ecls = nullptr;
     uint32_t *d_Tsw = nullptr;
     int *d_swoff = nullptr, *d_swlen = nullptr;
     int *d_canon = nullptr, *d_compact = nullptr;
@@ -313,14 +314,20 @@ sqa_status setup_program(sqa_handle *h)
 
     std::vector<SiteRec> sites, all_sites;
     std::vector<ETerm> et, all_et;
+    std::vector<EClass> ec, all_ec;
+    int n_ecls = 0;
+    bool ecls_ok = true;
     J.lut_entries = 0;
     for (int i = 0; i < pl.n; i++) J.lut_entries += 1 << ((int)pl.site_terms[i].size() + 2);
     for (int i = 0; i < h->I; i++) {
         const int32_t *Ji = h->J.data() + (size_t)i * npair;
         build_sites(pl, Ji, h->penalty, K, h->smax, sites);
         all_sites.insert(all_sites.end(), sites.begin(), sites.end());
-        build_eterms(pl, Ji, h->penalty, et);
+        const int nc = build_eterms(pl, Ji, h->penalty, et, ec);
+        if (nc == 0) ecls_ok = false;
+        n_ecls = std::max(n_ecls, nc);
         all_et.insert(all_et.end(), et.begin(), et.end());
+        all_ec.insert(all_ec.end(), ec.begin(), ec.end());
     }
     std::vector<uint32_t> T, Tsw;
     std::vector<int> swoff, swlen;
@@ -334,6 +341,8 @@ sqa_status setup_program(sqa_handle *h)
     if ((st = dalloc(h, &h->d_state, (size_t)h->I * J.Z * J.n * J.W)) != SQA_OK) return st;
     if ((st = upload(h, &h->d_sites, all_sites)) != SQA_OK) return st;
     if ((st = upload(h, &h->d_eterms, all_et)) != SQA_OK) return st;
+    if ((st = upload(h, &h->d_ecls, all_ec)) != SQA_OK) return st;
+    J.n_ecls = ecls_ok ? n_ecls : 0;
     if ((st = upload(h, &h->d_T, T)) != SQA_OK) return st;
     if (h->kind == SQA_KIND_PT) {
         if ((st = upload(h, &h->d_Tsw, Tsw)) != SQA_OK) return st;
@@ -353,6 +362,7 @@ sqa_status setup_program(sqa_handle *h)
     J.sites = h->d_sites;
     J.T = h->d_T;
     J.eterms = h->d_eterms;
+    J.ecls = h->d_ecls;
     J.Tsw = h->d_Tsw;
     J.sw_off = h->d_swoff;
     J.sw_len = h->d_swlen;

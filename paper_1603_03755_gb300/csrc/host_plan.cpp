@@ -205,7 +205,8 @@ void build_sites(const Plan &pl, const int32_t *J, int penalty, int K, int smax_
     }
 }
 
-void build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETerm> &out)
+int build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETerm> &out,
+                 std::vector<EClass> &cls)
 {
     out.clear();
     for (const PlanTerm &t : pl.terms) {
@@ -215,6 +216,29 @@ void build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETe
         e.size = t.size;
         out.push_back(e);
     }
+    std::stable_sort(out.begin(), out.end(), [](const ETerm &a, const ETerm &b) { return a.w < b.w; });
+    cls.assign(kMaxEClasses, EClass{0, 0, 0, 0});
+    int nc = 0, total = 0;
+    bool too_many = false;
+    for (size_t q = 0; q < out.size(); q++) {
+        total += out[q].w;
+        if (q == 0 || out[q].w != out[q - 1].w) {
+            if (nc == kMaxEClasses) {
+                too_many = true;
+                continue;
+            }
+            cls[nc] = EClass{out[q].w, (int32_t)q, 0, 0};
+            nc++;
+        }
+        if (!too_many) cls[nc - 1].count++;
+    }
+    cls[0].total = total;
+    if (too_many) {
+        for (auto &c : cls) c.count = 0;
+        cls[0].total = total;
+        return 0;
+    }
+    return nc;
 }
 
 // ---------------------------------------------------------------------------

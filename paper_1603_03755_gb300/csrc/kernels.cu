@@ -297,27 +297,80 @@ __device__ void build_luts(const JobDev &J, const Smem &sm)
     }
 }
 
-// PT: energies of every (slot, replica) of the unit, then the swap event.
-__device__ void pt_swap(const JobDev &J, const Smem &sm, int inst, int w0, int wc, int e)
+// PT: energies of every (slot, replica) of the unit.  E_b = sum_t w_t -
+// 2 sum_classes w_c n_c(b), where n_c(b) counts the terms of weight class c
+// whose value is negative for replica b.  One thread per (slot, word, class)
+// keeps n_c for all 32 replicas as a bit-sliced counter (plane k = bit k of
+// every replica's count), then adds -2 w_c n_c(b) into E.  Instances with too
+// many distinct weights fall back to a per-replica loop.
+__device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc)
 {
-    const int P = J.Z, n = J.n;
+    const int P = J.Z;
     const ETerm *et = J.eterms + (size_t)inst * J.n_eterms;
     const int nthr = blockDim.x;
+    if (J.n_ecls == 0) {
+        for (int it = threadIdx.x; it < P * wc * 32; it += nthr) {
+            const int b = it & 31, r = it >> 5, w = r % wc, p = r / wc;
+            const uint32_t *row = sm.S + (size_t)p * J.zstride;
+            int32_t E = 0;
+            for (int q = 0; q < J.n_eterms; q++) {
+                const ETerm x = et[q];
+                uint32_t v = row[x.m[0] * wc + w];
+                if (x.size > 1) v ^= row[x.m[1] * wc + w];
+                if (x.size > 2) v ^= row[x.m[2] * wc + w];
+                if (x.size > 3) v ^= row[x.m[3] * wc + w];
+                E += ((v >> b) & 1u) ? -x.w : x.w;
+            }
+            sm.E[(p * wc + w) * 32 + b] = E;
+        }
+        return;
+    }
+    const EClass *cls = J.ecls + (size_t)inst * kMaxEClasses;
+    const int total = cls[0].total;
+    for (int it = threadIdx.x; it < P * wc * 32; it += nthr) sm.E[it] = total;
     __syncthreads();
-    for (int it = threadIdx.x; it < P * wc * 32; it += nthr) {
-        const int b = it & 31, r = it >> 5, w = r % wc, p = r / wc;
+    const int nc = J.n_ecls;
+    for (int it = threadIdx.x; it < P * wc * nc; it += nthr) {
+        const int c = it % nc, r = it / nc, w = r % wc, p = r / wc;
+        const EClass k = cls[c];
+        if (k.count == 0) continue;
         const uint32_t *row = sm.S + (size_t)p * J.zstride;
-        int32_t E = 0;
-        for (int q = 0; q < J.n_eterms; q++) {
+        uint32_t cnt[12];
+#pragma unroll
+        for (int q = 0; q < 12; q++) cnt[q] = 0u;
+        for (int q = k.start; q < k.start + k.count; q++) {
             const ETerm x = et[q];
             uint32_t v = row[x.m[0] * wc + w];
             if (x.size > 1) v ^= row[x.m[1] * wc + w];
             if (x.size > 2) v ^= row[x.m[2] * wc + w];
             if (x.size > 3) v ^= row[x.m[3] * wc + w];
-            E += ((v >> b) & 1u) ? -x.w : x.w;
+            // add the bit vector v to the bit-sliced counter
+#pragma unroll
+            for (int q2 = 0; q2 < 12; q2++) {
+                const uint32_t carry = cnt[q2] & v;
+                cnt[q2] ^= v;
+                v = carry;
+            }
         }
-        sm.E[(p * wc + w) * 32 + b] = E;
+        int32_t *Ew = sm.E + (p * wc + w) * 32;
+        const int m2w = -2 * k.w;
+        for (int b = 0; b < 32; b++) {
+            int n = 0;
+#pragma unroll
+            for (int q2 = 0; q2 < 12; q2++) n |= (int)((cnt[q2] >> b) & 1u) << q2;
+            if (n) atomicAdd(Ew + b, m2w * n);
+        }
     }
+}
+
+// PT swap event e: slots (p, p+1) with p = e%2, e%2 + 2, ... exchange
+// configurations replica by replica (Eq. 9).
+__device__ void pt_swap(const JobDev &J, const Smem &sm, int inst, int w0, int wc, int e)
+{
+    const int P = J.Z, n = J.n;
+    const int nthr = blockDim.x;
+    __syncthreads();
+    pt_energies(J, sm, inst, wc);
     __syncthreads();
     const int p0 = e & 1;
     const int npairs = p0 + 1 < P ? (P - p0) / 2 : 0;

@@ -39,6 +39,16 @@ struct ETerm {
     int32_t size;
 };
 
+// Energy terms of one instance are sorted by weight; a class is a run of
+// terms with one weight.  Up to kMaxEClasses classes per instance.
+constexpr int kMaxEClasses = 16;
+struct EClass {
+    int32_t w;
+    int32_t start;
+    int32_t count;
+    int32_t total;  // class 0 only: sum of every term's weight (E of the all-up state)
+};
+
 // Device-side description of one job (one handle) for one launch.
 struct JobDev {
     int kind;        // SQA_KIND_SQA or SQA_KIND_PT
@@ -61,7 +71,8 @@ struct JobDev {
     uint32_t *state;     // [I][Z][n][W]
     const SiteRec *sites;    // [I][n]
     const uint32_t *T;       // SQA [S][nrow]; PT [P][nrow]
-    const ETerm *eterms;     // [I][n_eterms]
+    const ETerm *eterms;     // [I][n_eterms], sorted by weight
+    const EClass *ecls;      // [I][kMaxEClasses]; count 0 pads
     const uint32_t *Tsw;     // PT swap thresholds, dE = 1..sw_len[p]
     const int *sw_off;       // [P-1]
     const int *sw_len;       // [P-1]
@@ -70,7 +81,7 @@ struct JobDev {
     int smem_bytes;  // shared memory of one unit
     int lut_entries; // SQA: sum over sites of 2^(nterm+2)
     int use_lut;     // SQA: 1 = per-site code tables, 0 = byte-wise index windows
-    int pad_;
+    int n_ecls;      // weight classes used (max over instances); 0 = too many distinct weights
 };
 
 // One unit of work: the words [w0, w0+wc) of one instance of one job.
@@ -119,7 +130,10 @@ bool build_plan(int emb, int N, Plan &out, std::string &err);
 void build_sites(const Plan &pl, const int32_t *J, int penalty, int K, int smax_all,
                  std::vector<SiteRec> &sites_out);
 int site_weight_sum_max(const Plan &pl, const int32_t *J, int penalty);
-void build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETerm> &out);
+// Energy terms sorted by weight and their classes; returns the number of
+// classes, or 0 when the instance has more than kMaxEClasses distinct weights.
+int build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETerm> &out,
+                 std::vector<EClass> &cls);
 
 double jperp(double beta, double A, int L);
 double sqa_x(double alpha, double jp, int delta, int m);
