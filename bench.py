@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged-batch and PT workloads")
     ap.add_argument("--pt-sweeps", type=int, default=100_000)
     ap.add_argument("--ragged-sweeps", type=int, default=10_000)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=200)
     return ap.parse_args()
 
 
@@ -213,7 +215,58 @@ def extra_workloads(pkg, stream, args):
         out[f"pt_{emb}"] = {"workload": c["name"] + f", 32 temperatures, {args.pt_sweeps} sweeps, swap every sweep",
                             "value": att / t, "unit": UNIT, "seconds": t, "launch": h.launch()}
         h.close()
+    if not args.no_serving:
+        out["serving"] = [serving_workload(pkg, args.capacity, load, args.serving_jobs) for load in (0.5, 0.8)]
     return out
+
+
+def job_attempts(j) -> int:
+    n = j["N"] * (math.ceil(j["N"] / 4) + 1) if j["embedding"] == "me" else j["N"] * (j["N"] - 1) // 2
+    Z = j["L"] if j["kind"] == "sqa" else len(j["betas"])
+    return n * Z * j["R"] * j["sweeps"]
+
+
+def serving_workload(pkg, capacity, load, n_jobs=200, seed=0):
+    """Poisson stream of SQA/PT jobs (ME or LHZ, N 6-40, L 16-128, sweeps
+    log-uniform 1e3-1e5, 1-256 replicas) at `load` x capacity attempts/s,
+    served with continuous batching under a 64 GiB budget.  Latency is
+    submit-to-done on the server's clock."""
+    jobs = W.serving_stream(n_jobs, seed)
+    att = np.array([job_attempts(j) for j in jobs], float)
+    rate = load * capacity / att.mean()                 # jobs per second
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, n_jobs)
+    srv = pkg.Server(64 << 30)
+    ids = []
+    t0 = time.perf_counter()
+    t_next = 0.0
+    for j, gap in zip(jobs, gaps):
+        t_next += gap
+        delay = t0 + t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        kw = {k: j[k] for k in ("embedding", "N", "J", "penalty", "sweeps", "R", "seed", "kind")}
+        if j["kind"] == "sqa":
+            kw.update(L=j["L"], beta=j["beta"])
+        else:
+            kw.update(betas=j["betas"], swap_every=j["swap_every"])
+        ids.append(srv.submit(**kw))
+    infos = []
+    for jid in ids:
+        srv.wait(jid, timeout=900)
+        infos.append(srv.poll(jid))
+    st = srv.stats()
+    srv.close()
+    lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
+    qwait = np.array([i["t_start"] - i["t_submit"] for i in infos])
+    span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    done = [i["state"] == "done" for i in infos]
+    return {"offered_load": load, "jobs": n_jobs, "jobs_done": int(sum(done)),
+            "arrival_rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "p50_queue_s": float(np.percentile(qwait, 50)),
+            "attempts_per_s": float(att[np.array(done)].sum() / span), "makespan_s": span,
+            "epochs": st["epochs"], "graphs_built": st["graphs_built"], "max_resident_jobs": st["max_resident"],
+            "worker_s": {"admit": st["admit_s"], "epoch": st["epoch_s"], "retire": st["retire_s"]},
+            "failed_status": sorted({int(i["status"]) for i in infos if i["state"] != "done"})}
 
 
 def run_reference(args, cfg, world, rank, dist):
@@ -375,6 +428,7 @@ def main():
     intpeak = {k: round(pkg.int_peak(k), 2) for k in pkg.INT_PEAK_KINDS}
     t_sweep = statistics.mean(sweep_times)
     achieved_gops = attempts * OPS_PER_ATTEMPT / t_sweep / 1e9
+    args.capacity = value / world
     extra = None if args.no_extra else extra_workloads(pkg, stream, args)
     cpu = None
     if not args.no_cpu_baseline:
@@ -402,6 +456,9 @@ def main():
                               "batched_over_per_instance": value / world / per_inst_rate},
         "peaks_source": src,
         "other_workloads": extra,
+        "latency": None if not extra or "serving" not in extra else {
+            f"load_{int(100 * x['offered_load'])}pct": {"p50_s": x["p50_latency_s"], "p99_s": x["p99_latency_s"]}
+            for x in extra["serving"]},
         "launch": h.launch(),
     }
     print(json.dumps(out))

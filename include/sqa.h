@@ -113,14 +113,17 @@ void sqa_destroy(sqa_handle *h);
 sqa_status sqa_get_info(const sqa_handle *h, sqa_info *out);
 
 /* Launch shape of the sweep kernel (the autotuner's knobs; results do not
- * depend on them).  words_per_unit: 32-replica words one block holds
+ * depend on them).  words_per_unit: 32-replica words one unit holds
  * (0 = automatic).  use_table: SQA threshold lookup through per-site code
  * tables (1), byte-wise index windows (0), or automatic (-1); PT always uses
- * windows.  Fails with SQA_ERR_UNSUPPORTED, leaving the shape unchanged, when
- * the request does not fit in shared memory.  Synchronizes the device. */
-sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table);
+ * windows.  cluster: blocks per unit, 1, 2, 4 or 8 (0 = automatic); with
+ * C > 1 a thread-block cluster sweeps one unit, each block holding Z/C
+ * consecutive slices (SQA, C must divide L/2) or slots (PT, C must divide
+ * P).  Fails with SQA_ERR_UNSUPPORTED, leaving the shape unchanged, when the
+ * request does not fit.  Synchronizes the device. */
+sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, int32_t cluster);
 sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t *use_table,
-                          int32_t *smem_bytes);
+                          int32_t *smem_bytes, int32_t *cluster);
 
 /* Runs the whole program: fresh initial spins, then sweeps 0..S-1 (SQA
  * anneal, or PT with swaps every swap_every sweeps), as one persistent
@@ -185,6 +188,46 @@ sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, i
 sqa_status sqa_ground_energy_noalloc(int32_t N, int32_t n_instances, const int32_t *J_dev,
                                      int64_t *e_dev, void *stream);
 
+/* ---- serving: continuous batching of SQA and PT jobs ---- */
+
+typedef struct sqa_server sqa_server;
+typedef enum { SQA_JOB_QUEUED = 0, SQA_JOB_RUNNING = 1, SQA_JOB_DONE = 2, SQA_JOB_FAILED = 3 } sqa_job_state;
+typedef struct {
+    int32_t state;         /* sqa_job_state */
+    int32_t status;        /* sqa_status of a failed job */
+    double t_submit, t_start, t_done; /* seconds on the server's clock */
+    int64_t device_bytes;  /* device memory the job held while resident */
+} sqa_job_info;
+typedef struct {
+    int64_t jobs_submitted, jobs_done, jobs_failed, epochs, graphs_built, attempts;
+    int64_t resident, queued, max_resident, bytes_in_use, max_bytes;
+    double admit_s, epoch_s, retire_s; /* worker wall time in each phase */
+    int32_t worker_status, pad_;
+} sqa_server_stats;
+
+/* A server owns a worker thread that serves jobs on the current device.  At
+ * each epoch boundary it admits queued jobs in arrival order while their
+ * device memory fits mem_budget_bytes (a job larger than the budget fails
+ * with SQA_ERR_NOMEM), runs one launch in which every resident job advances
+ * its own sweeps (about unit_attempts_per_epoch attempts per block; 0 picks
+ * a default), and retires finished jobs (state and energies copied to host,
+ * device memory freed).  Results are bit-identical to sqa_run of the same
+ * descriptor, whatever else was resident. */
+sqa_status sqa_server_create(int64_t mem_budget_bytes, int64_t unit_attempts_per_epoch, sqa_server **out);
+/* Copies desc (kind SQA or PT) and queues it; thread-safe. */
+sqa_status sqa_server_submit(sqa_server *s, const sqa_desc *desc, uint64_t *job_id);
+sqa_status sqa_server_poll(sqa_server *s, uint64_t job_id, sqa_job_info *info);
+/* Blocks until the job is done or failed; SQA_ERR_TIMEOUT after timeout_s. */
+sqa_status sqa_server_wait(sqa_server *s, uint64_t job_id, double timeout_s);
+/* Host outputs of a done job: state [I][Z][n_phys][W], energies [I][Z][R]
+ * (either may be NULL).  SQA_ERR_BUSY while the job is pending. */
+sqa_status sqa_server_result(sqa_server *s, uint64_t job_id, uint32_t *state_out, int32_t *energies_out);
+/* Forgets a done or failed job. */
+sqa_status sqa_server_release(sqa_server *s, uint64_t job_id);
+sqa_status sqa_server_get_stats(sqa_server *s, sqa_server_stats *out);
+/* Stops the worker after its current epoch; frees every job. */
+void sqa_server_destroy(sqa_server *s);
+
 /* ---- host-only views of the library's planning (no device needed) ---- */
 
 /* The physical problem the library builds for one instance (Sec. II A/B):
@@ -195,6 +238,11 @@ sqa_status sqa_plan_terms(int32_t embedding, int32_t N, const int32_t *J, int32_
                           int32_t cap_terms, int32_t *n_phys, int32_t *n_terms,
                           int32_t *term_size, int32_t *term_mem, int32_t *term_w,
                           int32_t *colour);
+
+/* Device bytes sqa_create allocates for desc (the admission estimate of the
+ * serving loop): exact except the work-unit list, counted as one unit per
+ * 32-replica word, so an upper bound.  Host only; 0 on an invalid desc. */
+int64_t sqa_plan_device_bytes(const sqa_desc *desc);
 
 /* The acceptance thresholds sqa_create would upload for desc: SQA
  * [S][nd][3] indexed by ((delta - dmin)/2, (m + 2)/2), PT [P][nd] indexed

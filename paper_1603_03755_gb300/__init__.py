@@ -53,8 +53,9 @@ _SIGS = {
     "sqa_create": (C.c_int, [C.POINTER(_Desc), C.POINTER(C.c_void_p)]),
     "sqa_destroy": (None, [C.c_void_p]),
     "sqa_get_info": (C.c_int, [C.c_void_p, C.POINTER(_Info)]),
-    "sqa_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
-    "sqa_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "sqa_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "sqa_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_int32)]),
     "sqa_run": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sqa_run_sweeps": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     "sqa_run_per_instance": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -73,6 +74,15 @@ _SIGS = {
     "sqa_plan_swap_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
     "sqa_plan_tree": (C.c_int, [C.c_int32, C.c_uint64, C.c_int32, C.c_int32, C.c_void_p]),
     "sqa_int_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
+    "sqa_server_create": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_void_p)]),
+    "sqa_server_submit": (C.c_int, [C.c_void_p, C.POINTER(_Desc), C.POINTER(C.c_uint64)]),
+    "sqa_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
+    "sqa_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_double]),
+    "sqa_server_result": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "sqa_server_release": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "sqa_server_get_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sqa_server_destroy": (None, [C.c_void_p]),
+    "sqa_plan_device_bytes": (C.c_int64, [C.POINTER(_Desc)]),
     "sqa_strerror": (C.c_char_p, [C.c_int]),
     "sqa_last_error": (C.c_char_p, []),
 }
@@ -119,33 +129,53 @@ def _ptr(x):
     return x.data_ptr(), int(x.is_cuda)
 
 
+def _make_desc(*, embedding: str, N: int, J, penalty: int, sweeps: int, R: int, seed: int = 0,
+               kind: str = "sqa", L: int = 32, beta: float = 1.0, A=None, B=None, betas=None,
+               swap_every: int = 1):
+    """An sqa_desc and the arrays it points into (keep them alive)."""
+    J = np.ascontiguousarray(np.atleast_2d(np.asarray(J, np.int32)))
+    keep = [J]
+    d = _Desc()
+    d.kind, d.embedding, d.n_logical, d.n_instances = KIND[kind], EMB[embedding], N, J.shape[0]
+    d.J = J.ctypes.data
+    d.h = None
+    d.penalty, d.n_sweeps, d.n_replicas, d.seed = int(penalty), int(sweeps), int(R), int(seed)
+    d.n_slices, d.beta = int(L), float(beta)
+    if A is not None:
+        A = np.ascontiguousarray(A, np.float64)
+        B = np.ascontiguousarray(B, np.float64)
+        keep += [A, B]
+        d.A, d.B = A.ctypes.data, B.ctypes.data
+    if betas is not None:
+        betas = np.ascontiguousarray(betas, np.float64)
+        keep.append(betas)
+        d.betas, d.n_temps = betas.ctypes.data, len(betas)
+    d.swap_every = int(swap_every)
+    meta = {"N": N, "I": J.shape[0], "R": int(R), "kind": kind, "embedding": embedding,
+            "Z": int(L) if kind == "sqa" else (len(betas) if betas is not None else 0)}
+    return d, keep, meta
+
+
+def plan_n_phys(embedding: str, N: int) -> int:
+    """Canonical physical sites of an embedding of K_N (host only)."""
+    return 8 * ((N + 3) // 4) ** 2 if embedding == "me" else N * (N - 1) // 2
+
+
+def plan_device_bytes(**kw) -> int:
+    """Device bytes sqa_create would allocate (host only)."""
+    d, keep, _ = _make_desc(**kw)
+    return int(lib().sqa_plan_device_bytes(C.byref(d)))
+
+
 class Handle:
     """One problem (I instances sharing every parameter but J) and its
     resident device state.  ``kind`` 'sqa' or 'pt'; ``embedding`` 'me' or
     'lhz'.  J has shape [I, N(N-1)/2] (int32)."""
 
-    def __init__(self, *, embedding: str, N: int, J, penalty: int, sweeps: int, R: int,
-                 seed: int = 0, kind: str = "sqa", L: int = 32, beta: float = 1.0, A=None, B=None,
-                 betas=None, swap_every: int = 1):
-        J = np.ascontiguousarray(np.atleast_2d(np.asarray(J, np.int32)))
-        self.N, self.I, self.R, self.kind, self.embedding = N, J.shape[0], R, kind, embedding
-        self._keep = [J]
-        d = _Desc()
-        d.kind, d.embedding, d.n_logical, d.n_instances = KIND[kind], EMB[embedding], N, self.I
-        d.J = J.ctypes.data
-        d.h = None
-        d.penalty, d.n_sweeps, d.n_replicas, d.seed = int(penalty), int(sweeps), int(R), int(seed)
-        d.n_slices, d.beta = int(L), float(beta)
-        if A is not None:
-            A = np.ascontiguousarray(A, np.float64)
-            B = np.ascontiguousarray(B, np.float64)
-            self._keep += [A, B]
-            d.A, d.B = A.ctypes.data, B.ctypes.data
-        if betas is not None:
-            betas = np.ascontiguousarray(betas, np.float64)
-            self._keep.append(betas)
-            d.betas, d.n_temps = betas.ctypes.data, len(betas)
-        d.swap_every = int(swap_every)
+    def __init__(self, **kw):
+        d, keep, meta = _make_desc(**kw)
+        self.N, self.I, self.R, self.kind, self.embedding = meta["N"], meta["I"], meta["R"], meta["kind"], meta["embedding"]
+        self._keep = keep
         h = C.c_void_p()
         _check(lib().sqa_create(C.byref(d), C.byref(h)), "sqa_create")
         self._h = h
@@ -168,13 +198,15 @@ class Handle:
     __del__ = close
 
     # ---- launch shape ----
-    def tune(self, words_per_unit: int = 0, use_table: int = -1):
-        _check(lib().sqa_tune(self._h, words_per_unit, use_table), "sqa_tune")
+    def tune(self, words_per_unit: int = 0, use_table: int = -1, cluster: int = 0):
+        _check(lib().sqa_tune(self._h, words_per_unit, use_table, cluster), "sqa_tune")
 
     def launch(self) -> dict:
-        wc, lut, smem = C.c_int32(), C.c_int32(), C.c_int32()
-        _check(lib().sqa_get_launch(self._h, C.byref(wc), C.byref(lut), C.byref(smem)), "sqa_get_launch")
-        return {"words_per_unit": wc.value, "use_table": lut.value, "smem_bytes": smem.value}
+        wc, lut, smem, cl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().sqa_get_launch(self._h, C.byref(wc), C.byref(lut), C.byref(smem), C.byref(cl)),
+               "sqa_get_launch")
+        return {"words_per_unit": wc.value, "use_table": lut.value, "smem_bytes": smem.value,
+                "cluster": cl.value}
 
     # ---- running ----
     def run(self, stream=None):
@@ -237,6 +269,77 @@ class Handle:
                                 succ.ctypes.data if eg is not None else None, 0, _stream_ptr(stream)),
                "sqa_decode")
         return logical, energy, (succ if eg is not None else None)
+
+
+class _JobInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_done", C.c_double), ("device_bytes", C.c_int64)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("jobs_submitted", "jobs_done", "jobs_failed", "epochs", "graphs_built",
+                                         "attempts", "resident", "queued", "max_resident", "bytes_in_use",
+                                         "max_bytes")] + [("admit_s", C.c_double), ("epoch_s", C.c_double),
+                                                          ("retire_s", C.c_double), ("worker_status", C.c_int32),
+                                                          ("pad_", C.c_int32)]
+
+
+JOB_STATES = ("queued", "running", "done", "failed")
+
+
+class Server:
+    """Continuous-batching server on the current CUDA device (a worker thread
+    in the library).  submit() takes the same keywords as Handle."""
+
+    def __init__(self, mem_budget_bytes: int, unit_attempts_per_epoch: int = 0):
+        s = C.c_void_p()
+        _check(lib().sqa_server_create(int(mem_budget_bytes), int(unit_attempts_per_epoch), C.byref(s)),
+               "sqa_server_create")
+        self._s = s
+        self._meta = {}
+
+    def submit(self, **kw) -> int:
+        d, keep, meta = _make_desc(**kw)
+        jid = C.c_uint64()
+        _check(lib().sqa_server_submit(self._s, C.byref(d), C.byref(jid)), "sqa_server_submit")
+        meta["n_phys"] = plan_n_phys(meta["embedding"], meta["N"])
+        self._meta[jid.value] = meta
+        return jid.value
+
+    def poll(self, job_id: int) -> dict:
+        info = _JobInfo()
+        _check(lib().sqa_server_poll(self._s, job_id, C.byref(info)), "sqa_server_poll")
+        out = {k: getattr(info, k) for k, _ in _JobInfo._fields_}
+        out["state"] = JOB_STATES[out["state"]]
+        return out
+
+    def wait(self, job_id: int, timeout: float = 600.0):
+        _check(lib().sqa_server_wait(self._s, job_id, float(timeout)), "sqa_server_wait")
+
+    def result(self, job_id: int):
+        """(state [I, Z, n_phys, W] uint32, energies [I, Z, R] int32)."""
+        m = self._meta[job_id]
+        W = (m["R"] + 31) // 32
+        st = np.zeros((m["I"], m["Z"], m["n_phys"], W), np.uint32)
+        en = np.zeros((m["I"], m["Z"], m["R"]), np.int32)
+        _check(lib().sqa_server_result(self._s, job_id, st.ctypes.data, en.ctypes.data), "sqa_server_result")
+        return st, en
+
+    def release(self, job_id: int):
+        _check(lib().sqa_server_release(self._s, job_id), "sqa_server_release")
+        self._meta.pop(job_id, None)
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().sqa_server_get_stats(self._s, C.byref(st)), "sqa_server_get_stats")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_ if k != "pad_"}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().sqa_server_destroy(self._s)
+            self._s = None
+
+    __del__ = close
 
 
 def batch_run(handles, stream=None):

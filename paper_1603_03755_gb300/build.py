@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsqa_gb300.so")
-SOURCES = ("kernels.cu", "capi.cu", "host_plan.cpp", "intpeak.cu", "noalloc.cu")
-HEADERS = ("philox.cuh", "sqa_internal.h")
+SOURCES = ("kernels.cu", "capi.cu", "host_plan.cpp", "intpeak.cu", "noalloc.cu", "server.cu")
+HEADERS = ("philox.cuh", "sqa_internal.h", "layout.cuh", "handle.h")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -65,7 +65,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], capture_output=True, text=True)
+    r = subprocess.run([cc, ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs, "-lcudart"],
+                       capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "handle.h"
 #include "layout.cuh"
 #include "philox.cuh"
 #include "sqa_internal.h"
@@ -21,6 +22,7 @@ const void *sweep_one_entry(const JobDev &J);
 const void *sweep_one_entry_mode(int mode);
 cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, int *counter, int grid,
                              cudaStream_t s);
+int max_active_clusters(const JobDev &J);
 static const void *one_kernel(const JobDev &J) { return sweep_one_entry(J); }
 __global__ void energy_kernel(JobDev J, int32_t *out);
 __global__ void canon_kernel(JobDev J, const int *compact_of, int z0, int zcount, uint32_t *out);
@@ -31,7 +33,7 @@ __global__ void ground_kernel(int N, const int32_t *J, int chunk_bits, int64_t n
 static thread_local std::string g_err;
 void set_error(const std::string &msg) { g_err = msg; }
 
-static sqa_status cuda_fail(cudaError_t e, const char *where)
+sqa_status cuda_fail(cudaError_t e, const char *where)
 {
     g_err = std::string(where) + ": " + cudaGetErrorString(e);
     return SQA_ERR_CUDA;
@@ -48,7 +50,7 @@ constexpr int kThreads = 256;
 static int g_num_sms = 0;
 static int g_smem_limit = 0;  // dynamic shared memory one sweep block may use
 
-static sqa_status device_ready()
+sqa_status device_ready()
 {
     int dev = 0, n = 0;
     cudaError_t e = cudaGetDeviceCount(&n);
@@ -81,40 +83,6 @@ static sqa_status device_ready()
 
 using namespace sqa;
 
-struct sqa_handle {
-    // copied description
-    int kind = 0, emb = 0, N = 0, I = 0, penalty = 0, S = 0, R = 0, L = 0, P = 0, swap_every = 1;
-    uint64_t seed = 0;
-    double beta = 0;
-    std::vector<int32_t> J;
-    std::vector<double> A, B, betas;
-    Plan plan;
-    int smax = 0, dmin = 0, dmax = 0, nd = 0;
-    bool window_limit_exceeded = false;
-    int force_wc = 0, force_mode = -1;  // sqa_tune overrides (0 / -1: automatic)
-    // device
-    JobDev job{};
-    uint32_t *d_state = nullptr;
-    SiteRec *d_sites = nullptr;
-    uint32_t *d_T = nullptr;
-    ETerm *d_eterms = nullptr;
-    EClass *d_ecls = nullptr;
-    uint32_t *d_Tsw = nullptr;
-    int *d_swoff = nullptr, *d_swlen = nullptr;
-    int *d_canon = nullptr, *d_compact = nullptr;
-    int32_t *d_J = nullptr;
-    int *d_chain = nullptr, *d_pair = nullptr;
-    int *d_parents = nullptr, *d_orders = nullptr;
-    int cur_trees = -1, cur_tree_kind = -1;
-    JobDev *d_job = nullptr;
-    Unit *d_units = nullptr;
-    int n_units = 0;
-    int *d_counter = nullptr;
-    std::vector<Unit> units;
-    int64_t device_bytes = 0;
-    int64_t h2d_bytes = 0;
-    std::vector<void *> allocs;
-};
 
 namespace {
 
@@ -189,49 +157,67 @@ int blocks_per_sm(const void *kernel, int smem)
     return per_sm;
 }
 
-// Choose the words per unit (and, for SQA, table or window mode): the most
-// resident blocks per SM first, then the most words per unit.
-sqa_status plan_units(sqa_handle *h)
+// Choose the launch shape of a job: blocks per unit (a cluster of C blocks
+// splitting the slices or slots), words per unit and, for SQA, table or
+// window mode.  Objective: the most blocks busy at once, counting a cluster's
+// blocks at 90 % (barriers and remote reads); then smaller C, table mode,
+// more words per unit.  c_forced > 0 restricts C.  Writes J's shape fields
+// and the unit list.
+sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> &units)
 {
-    JobDev &J = h->job;
-    int best_wc = 0, best_blocks = 0, best_lut = 0;
-    const int modes = J.kind == SQA_KIND_SQA ? 2 : 1;
-    for (int m = modes - 1; m >= 0; m--) {
-        J.use_lut = J.kind == SQA_KIND_SQA ? m : 0;
-        if (!J.use_lut && h->window_limit_exceeded) continue;
-        if (h->force_mode >= 0 && J.kind == SQA_KIND_SQA && J.use_lut != h->force_mode) continue;
-        for (int wc = J.W; wc >= 1; wc = wc > 1 ? (wc + 1) / 2 : 0) {
-            if (h->force_wc > 0 && wc != std::min(h->force_wc, J.W)) {
+    struct Best {
+        double score = -1;
+        int C = 0, wc = 0, lut = 0;
+    } best;
+    const int cmax = c_forced > 0 ? c_forced : 8;
+    for (int C = c_forced > 0 ? c_forced : 1; C <= cmax; C *= 2) {
+        if (J.kind == SQA_KIND_SQA ? (J.Z % (2 * C)) : (J.Z % C)) continue;
+        J.csize = C;
+        J.zr = J.Z / C;
+        const int modes = J.kind == SQA_KIND_SQA ? 2 : 1;
+        for (int m = modes - 1; m >= 0; m--) {
+            J.use_lut = J.kind == SQA_KIND_SQA ? m : 0;
+            if (!J.use_lut && h->window_limit_exceeded) continue;
+            if (h->force_mode >= 0 && J.kind == SQA_KIND_SQA && J.use_lut != h->force_mode) continue;
+            for (int wc = J.W; wc >= 1; wc = wc > 1 ? (wc + 1) / 2 : 0) {
+                const bool take = h->force_wc <= 0 || wc == std::min(h->force_wc, J.W);
+                if (take) {
+                    int zs = 0;
+                    const int smem = unit_smem(J, wc, &zs);
+                    if (smem <= g_smem_limit) {
+                        J.smem_bytes = smem;
+                        J.wc = wc;
+                        J.zstride = zs;
+                        const int active = C == 1 ? blocks_per_sm(one_kernel(J), smem) * g_num_sms
+                                                  : max_active_clusters(J);
+                        const int64_t n_units = (int64_t)h->I * ((J.W + wc - 1) / wc);
+                        const double busy = (double)std::min<int64_t>(n_units, active) * C * (C == 1 ? 1.0 : 0.9);
+                        const bool better = busy > best.score * 1.0001 ||
+                                            (busy >= best.score * 0.9999 && C == best.C &&
+                                             (J.use_lut > best.lut || (J.use_lut == best.lut && wc > best.wc)));
+                        if (active > 0 && better) best = Best{busy, C, wc, J.use_lut};
+                    }
+                }
                 if (wc == 1) break;
-                continue;
             }
-            int zs = 0;
-            const int smem = unit_smem(J, wc, &zs);
-            if (smem > g_smem_limit) continue;
-            J.smem_bytes = smem;
-            J.wc = wc;
-            J.zstride = zs;
-            const int blocks = std::min(blocks_per_sm(one_kernel(J), smem), 3);
-            if (blocks > best_blocks) {
-                best_blocks = blocks;
-                best_wc = wc;
-                best_lut = J.use_lut;
-            }
-            if (wc == 1) break;
         }
     }
-    if (best_blocks == 0) {
+    if (best.score <= 0) {
         set_error("the requested unit does not fit in shared memory");
         return SQA_ERR_UNSUPPORTED;
     }
-    J.use_lut = best_lut;
-    J.wc = best_wc;
-    J.smem_bytes = unit_smem(J, best_wc, &J.zstride);
-    h->units.clear();
+    J.csize = best.C;
+    J.zr = J.Z / best.C;
+    J.use_lut = best.lut;
+    J.wc = best.wc;
+    J.smem_bytes = unit_smem(J, best.wc, &J.zstride);
+    units.clear();
     for (int i = 0; i < h->I; i++)
-        for (int w0 = 0; w0 < J.W; w0 += J.wc) h->units.push_back(Unit{0, i, w0, std::min(J.wc, J.W - w0)});
+        for (int w0 = 0; w0 < J.W; w0 += J.wc) units.push_back(Unit{0, i, w0, std::min(J.wc, J.W - w0)});
     return SQA_OK;
 }
+
+sqa_status plan_units(sqa_handle *h) { return plan_shape(h, h->force_cluster, h->job, h->units); }
 
 sqa_status validate(const sqa_desc *d)
 {
@@ -304,6 +290,8 @@ sqa_status setup_program(sqa_handle *h)
     J.nrow = h->kind == SQA_KIND_SQA ? 3 * h->nd : h->nd;
     J.n_eterms = (int)pl.terms.size();
     J.swap_every = h->swap_every;
+    J.csize = 1;
+    J.zr = J.Z;
     J.t0 = 0;
     J.t1 = h->S;
     J.seed_lo = (uint32_t)h->seed;
@@ -374,28 +362,16 @@ sqa_status setup_program(sqa_handle *h)
     return SQA_OK;
 }
 
-sqa_status launch_init(sqa_handle *h, cudaStream_t s)
-{
-    const int64_t total = (int64_t)h->I * h->job.Z * h->job.n * h->job.W;
-    const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 4 * 1024);
-    init_kernel<<<std::max(blocks, 1), kThreads, 0, s>>>(h->job, h->d_canon);
-    SQA_CUDA(cudaGetLastError());
-    return SQA_OK;
-}
-
-int grid_for(const void *kernel, int smem_bytes, int n_units)
-{
-    int per_sm = std::max(blocks_per_sm(kernel, smem_bytes), 1);
-    return std::max(1, std::min(n_units, per_sm * g_num_sms));
-}
-
-// One launch of the sweep kernel over units [u0, u0+nu) of one handle.
 sqa_status launch_sweeps(sqa_handle *h, int t0, int t1, int u0, int nu, cudaStream_t s)
 {
     h->job.t0 = t0;
     h->job.t1 = t1;
     SQA_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
-    const int grid = grid_for(one_kernel(h->job), h->job.smem_bytes, nu);
+    int grid;
+    if (h->job.csize == 1)
+        grid = grid_for(one_kernel(h->job), h->job.smem_bytes, nu);
+    else
+        grid = std::max(1, std::min(nu, max_active_clusters(h->job))) * h->job.csize;
     SQA_CUDA(launch_sweep_one(h->job, h->d_units + u0, nu, h->d_counter, grid, s));
     return SQA_OK;
 }
@@ -425,6 +401,69 @@ sqa_status decode_trees(sqa_handle *h, int method, int n_trees)
 }
 
 }  // namespace
+
+namespace sqa {
+
+sqa_status launch_init(sqa_handle *h, cudaStream_t s)
+{
+    const int64_t total = (int64_t)h->I * h->job.Z * h->job.n * h->job.W;
+    const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 4 * 1024);
+    init_kernel<<<std::max(blocks, 1), kThreads, 0, s>>>(h->job, h->d_canon);
+    SQA_CUDA(cudaGetLastError());
+    return SQA_OK;
+}
+
+int grid_for(const void *kernel, int smem_bytes, int n_units)
+{
+    int per_sm = std::max(blocks_per_sm(kernel, smem_bytes), 1);
+    return std::max(1, std::min(n_units, per_sm * g_num_sms));
+}
+
+// One launch of the sweep kernel over units [u0, u0+nu) of one handle.
+int64_t estimate_device_bytes(const sqa_desc *d)
+{
+    if (validate(d) != SQA_OK) return 0;
+    Plan pl;
+    std::string err;
+    if (!build_plan(d->embedding, d->n_logical, pl, err)) return 0;
+    const int N = d->n_logical, I = d->n_instances, npair = N * (N - 1) / 2;
+    int smax = 0;
+    for (int i = 0; i < I; i++) smax = std::max(smax, site_weight_sum_max(pl, d->J + (size_t)i * npair, d->penalty));
+    const int64_t nd = 2 * smax + 1;
+    const int64_t Z = d->kind == SQA_KIND_SQA ? d->n_slices : d->n_temps;
+    const int64_t W = (d->n_replicas + 31) / 32;
+    const auto al = [](int64_t b) { return std::max<int64_t>(b, 1); };
+    int64_t b = 0;
+    b += al((int64_t)I * Z * pl.n * W * 4);                          // state
+    b += al((int64_t)I * pl.n * (int64_t)sizeof(SiteRec));           // site records
+    b += al((int64_t)I * (int64_t)pl.terms.size() * (int64_t)sizeof(ETerm));
+    b += al((int64_t)I * kMaxEClasses * (int64_t)sizeof(EClass));
+    if (d->kind == SQA_KIND_SQA) {
+        b += al((int64_t)d->n_sweeps * 3 * nd * 4);                  // thresholds
+    } else {
+        b += al((int64_t)d->n_temps * nd * 4);
+        std::vector<uint32_t> T;
+        std::vector<int> off, len;
+        swap_tables(d->betas, d->n_temps, T, off, len);
+        b += al((int64_t)T.size() * 4) + 2 * al((int64_t)off.size() * 4);
+    }
+    b += al((int64_t)pl.canon.size() * 4) + al((int64_t)pl.compact.size() * 4) + al((int64_t)I * npair * 4);
+    b += d->embedding == SQA_EMB_ME_CHIMERA ? al((int64_t)pl.chain.size() * 4) : al((int64_t)pl.pair.size() * 4);
+    b += al((int64_t)sizeof(JobDev)) + al((int64_t)I * W * (int64_t)sizeof(Unit)) + al(4);
+    return b;
+}
+
+cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s)
+{
+    int grid;
+    if (J.csize == 1)
+        grid = grid_for(sweep_one_entry(J), J.smem_bytes, n_units);
+    else
+        grid = std::max(1, std::min(n_units, max_active_clusters(J))) * J.csize;
+    return launch_sweep_one(J, units, n_units, counter, grid, s);
+}
+
+}  // namespace sqa
 
 extern "C" {
 
@@ -492,7 +531,9 @@ sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
     st = setup_program(h);
     if (st == SQA_OK) st = launch_init(h, 0);
     if (st == SQA_OK) {
-        cudaError_t e = cudaDeviceSynchronize();
+        // the legacy stream: waits for this handle's work only, not for work
+        // on non-blocking streams (a serving loop's running epoch)
+        cudaError_t e = cudaStreamSynchronize(0);
         if (e != cudaSuccess) st = cuda_fail(e, "sqa_create");
     }
     if (st != SQA_OK) {
@@ -530,19 +571,23 @@ sqa_status sqa_get_info(const sqa_handle *h, sqa_info *o)
     return SQA_OK;
 }
 
-sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table)
+sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, int32_t cluster)
 {
-    if (!h || words_per_unit < 0 || use_table < -1 || use_table > 1) return set_error("tune arguments"), SQA_ERR_INVALID;
+    if (!h || words_per_unit < 0 || use_table < -1 || use_table > 1 || cluster < 0 || cluster > 8 ||
+        (cluster & (cluster - 1)))
+        return set_error("tune arguments"), SQA_ERR_INVALID;
     if (use_table == 0 && h->window_limit_exceeded) return set_error("window mode cannot hold this problem"), SQA_ERR_UNSUPPORTED;
-    const int old_wc = h->force_wc, old_mode = h->force_mode;
+    const int old_wc = h->force_wc, old_mode = h->force_mode, old_c = h->force_cluster;
     h->force_wc = words_per_unit;
     h->force_mode = use_table;
+    h->force_cluster = cluster;
     const JobDev keep = h->job;
     const std::vector<Unit> keep_units = h->units;
     sqa_status st = plan_units(h);
     if (st != SQA_OK) {
         h->force_wc = old_wc;
         h->force_mode = old_mode;
+        h->force_cluster = old_c;
         h->job = keep;
         h->units = keep_units;
         return st;
@@ -558,12 +603,14 @@ sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table)
     return SQA_OK;
 }
 
-sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t *use_table, int32_t *smem_bytes)
+sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t *use_table, int32_t *smem_bytes,
+                          int32_t *cluster)
 {
     if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
     if (words_per_unit) *words_per_unit = h->job.wc;
     if (use_table) *use_table = h->job.use_lut;
     if (smem_bytes) *smem_bytes = h->job.smem_bytes;
+    if (cluster) *cluster = h->job.csize;
     return SQA_OK;
 }
 
@@ -632,12 +679,16 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
         sqa_handle *h = hs[k];
         if (!h) return set_error("NULL handle in batch"), SQA_ERR_INVALID;
         if ((st = launch_init(h, s)) != SQA_OK) return st;
+        // the multi-job kernel runs every unit in one block: plan each job
+        // for a single block per unit
         JobDev J = h->job;
+        std::vector<Unit> ju;
+        if ((st = plan_shape(h, 1, J, ju)) != SQA_OK) return st;
         J.t0 = 0;
         J.t1 = h->S;
         jobs.push_back(J);
         smem = std::max(smem, J.smem_bytes);
-        for (Unit u : h->units) {
+        for (Unit u : ju) {
             u.job = k;
             units.push_back(u);
         }
@@ -844,6 +895,8 @@ sqa_status sqa_plan_terms(int32_t embedding, int32_t N, const int32_t *J, int32_
     }
     return SQA_OK;
 }
+
+int64_t sqa_plan_device_bytes(const sqa_desc *d) { return estimate_device_bytes(d); }
 
 sqa_status sqa_plan_tables(const sqa_desc *d, uint32_t *T, int64_t cap, int32_t *dmin_out,
                            int32_t *dmax_out)

@@ -1,0 +1,60 @@
+// The handle behind the C ABI's opaque sqa_handle, and the internal entry
+// points shared by the C ABI (capi.cu) and the serving loop (server.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "sqa_internal.h"
+
+struct sqa_handle {
+    // copied description
+    int kind = 0, emb = 0, N = 0, I = 0, penalty = 0, S = 0, R = 0, L = 0, P = 0, swap_every = 1;
+    uint64_t seed = 0;
+    double beta = 0;
+    std::vector<int32_t> J;
+    std::vector<double> A, B, betas;
+    sqa::Plan plan;
+    int smax = 0, dmin = 0, dmax = 0, nd = 0;
+    bool window_limit_exceeded = false;
+    int force_wc = 0, force_mode = -1, force_cluster = 0;  // sqa_tune overrides (0 / -1: automatic)
+    // device
+    sqa::JobDev job{};
+    uint32_t *d_state = nullptr;
+    sqa::SiteRec *d_sites = nullptr;
+    uint32_t *d_T = nullptr;
+    sqa::ETerm *d_eterms = nullptr;
+    sqa::EClass *d_ecls = nullptr;
+    uint32_t *d_Tsw = nullptr;
+    int *d_swoff = nullptr, *d_swlen = nullptr;
+    int *d_canon = nullptr, *d_compact = nullptr;
+    int32_t *d_J = nullptr;
+    int *d_chain = nullptr, *d_pair = nullptr;
+    int *d_parents = nullptr, *d_orders = nullptr;
+    int cur_trees = -1, cur_tree_kind = -1;
+    sqa::JobDev *d_job = nullptr;
+    sqa::Unit *d_units = nullptr;
+    int n_units = 0;
+    int *d_counter = nullptr;
+    std::vector<sqa::Unit> units;
+    int64_t device_bytes = 0;
+    int64_t h2d_bytes = 0;
+    std::vector<void *> allocs;
+};
+
+
+namespace sqa {
+
+sqa_status device_ready();
+sqa_status cuda_fail(cudaError_t e, const char *where);
+// Draws fresh initial spins for every instance of h on stream s.
+sqa_status launch_init(sqa_handle *h, cudaStream_t s);
+// Blocks for one launch of kernel over n_units units (at most one wave).
+int grid_for(const void *kernel, int smem_bytes, int n_units);
+// The multi-job sweep kernel (kernels.cu).
+__global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units, int *counter);
+// Device bytes sqa_create would allocate for desc (host-only estimate, exact
+// for the state and tables).
+int64_t estimate_device_bytes(const sqa_desc *d);
+
+}  // namespace sqa

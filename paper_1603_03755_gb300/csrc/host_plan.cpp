@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <thread>
 
 #include "philox.cuh"
 #include "sqa_internal.h"
@@ -267,6 +268,9 @@ double sqa_x(double alpha, double jp, int delta, int m)
 uint32_t threshold(double x)
 {
     if (x <= 0.0) return 0xFFFFFFFFu;
+    // 2^32 e^-x < 0.44 for x >= 23, so the floor is 0 whatever the last bit
+    // of exp: skip the call
+    if (x >= 23.0) return 0u;
     const double v = floor(ldexp(exp(-x), 32));
     if (v >= 4294967294.0) return 0xFFFFFFFEu;
     return (uint32_t)v;
@@ -277,13 +281,29 @@ void sqa_tables(const double *A, const double *B, double beta, int L, int S, int
 {
     const int nd = (dmax - dmin) / 2 + 1;
     T.assign((size_t)S * nd * 3, 0);
-    for (int t = 0; t < S; t++) {
-        const double alpha = beta * B[t] / (double)L;
-        const double jp = jperp(beta, A[t], L);
-        for (int di = 0; di < nd; di++)
-            for (int mi = 0; mi < 3; mi++)
-                T[((size_t)t * nd + di) * 3 + mi] = threshold(sqa_x(alpha, jp, dmin + 2 * di, 2 * mi - 2));
+    auto rows = [&](int t0, int t1) {
+        for (int t = t0; t < t1; t++) {
+            const double alpha = beta * B[t] / (double)L;
+            const double jp = jperp(beta, A[t], L);
+            for (int di = 0; di < nd; di++)
+                for (int mi = 0; mi < 3; mi++)
+                    T[((size_t)t * nd + di) * 3 + mi] = threshold(sqa_x(alpha, jp, dmin + 2 * di, 2 * mi - 2));
+        }
+    };
+    // rows are independent: large tables are built by several host threads
+    const int64_t work = (int64_t)S * nd * 3;
+    int nthr = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+    if (work < (1 << 20)) nthr = 1;
+    if (nthr == 1) {
+        rows(0, S);
+        return;
     }
+    std::vector<std::thread> pool;
+    for (int k = 0; k < nthr; k++) {
+        const int t0 = (int)((int64_t)S * k / nthr), t1 = (int)((int64_t)S * (k + 1) / nthr);
+        pool.emplace_back(rows, t0, t1);
+    }
+    for (auto &th : pool) th.join();
 }
 
 void pt_tables(const double *betas, int P, int dmin, int dmax, std::vector<uint32_t> &T)

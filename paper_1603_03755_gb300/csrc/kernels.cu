@@ -21,6 +21,7 @@
 // loads the four thresholds and compares them with the high 16 bits of the
 // replicas' uniforms; only when those bits tie with the threshold's high
 // half is the low half drawn (probability 2^-16).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -62,15 +63,25 @@ __global__ void init_kernel(JobDev J, const int *canon)
 
 // ---------------------------------------------------------------------------
 // The persistent sweep kernel.
+//
+// A unit (one instance's run of words) is swept by a cluster of C blocks
+// (C = 1, 2, 4 or 8).  Block rank r owns the contiguous slices (SQA) or
+// temperature slots (PT) [r*zr, (r+1)*zr), zr = Z/C, in its shared memory.
+// SQA reads the temporal neighbours of its first and last slice from the
+// neighbouring blocks' shared memory and separates colour phases with a
+// cluster barrier; PT slots never interact within a sweep, and swap events
+// exchange the boundary slots' energies and words across blocks.
 // ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
 struct Smem {
-    uint32_t *S;      // [Z][zstride]
-    uint32_t *T;      // full thresholds: SQA one row, PT P rows
-    int32_t *Tq;      // PT: -(T high half << 15), P rows
-    int32_t *lut;     // SQA: per-site tables, -(T high half << 15) by code
+    uint32_t *S;      // [zr][zstride]
+    uint32_t *T;      // full thresholds: SQA one row, PT zr rows
+    int32_t *Tq;      // -(T high half << 15): PT zr rows, SQA window mode one row
+    int32_t *lut;     // SQA table mode: per-site tables by code
     SiteRec *sites;   // [n]
-    int32_t *E;       // PT: [P][wc*32]
-    uint32_t *M;      // PT: swap masks [P/2+1][wc]
+    int32_t *E;       // PT: [zr][wc*32]
+    uint32_t *M;      // PT: swap masks [zr/2+1][wc]
 };
 
 __device__ __forceinline__ Smem carve(const JobDev &J, unsigned char *base)
@@ -85,6 +96,22 @@ __device__ __forceinline__ Smem carve(const JobDev &J, unsigned char *base)
     m.E = (int32_t *)(base + o.E);
     m.M = (uint32_t *)(base + o.M);
     return m;
+}
+
+// The block's place in its cluster, and the neighbouring blocks' slices
+// next to its own (SQA temporal neighbours across the block boundary).
+struct Part {
+    int C, rank, z0, zr;
+    const uint32_t *up;  // slice z0 - 1 (the previous block's last slice)
+    const uint32_t *dn;  // slice z0 + zr (the next block's first slice)
+};
+
+__device__ __forceinline__ void cluster_barrier(int C)
+{
+    if (C > 1)
+        cg::this_cluster().sync();
+    else
+        __syncthreads();
 }
 
 // Negated high half of a threshold, scaled to 31 bits: for a 31-bit value x
@@ -116,7 +143,7 @@ __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *r
     }
 }
 
-// PT threshold index bytes of replicas (j, j+8, j+16, j+24): sum of K*|w| over
+// Threshold index bytes of replicas (j, j+8, j+16, j+24): sum of K*|w| over
 // the terms that turn positive, added byte-wise.
 __device__ __forceinline__ uint32_t window4(const uint32_t (&pl)[kMaxTerms],
                                             const uint32_t (&kw)[kMaxTerms], int j)
@@ -179,8 +206,8 @@ struct Keys {
     uint32_t k0, khi, klo;
 };
 
-// Full threshold index of replica (r, j) from its code (SQA: bit 0, 1 = the
-// two temporal disagreements, bit 2+k = term k negative) or PT index byte.
+// Full threshold index of a replica from its code (SQA tables: bit 0, 1 = the
+// two temporal disagreements, bit 2+k = term k negative) or its window byte.
 template <int KIND>
 __device__ __forceinline__ int full_index(const SiteRec &sr, uint32_t code)
 {
@@ -197,28 +224,37 @@ __device__ __forceinline__ int full_index(const SiteRec &sr, uint32_t code)
     return sr.base + (int)code;
 }
 
-// One item: the word of 32 replicas of site si at slice/slot z.  Byte r of
-// code[j] selects replica j + 8r's threshold: a per-site table entry (SQA,
+// One item: the word of 32 replicas of site si at local slice/slot zl.  Byte r
+// of code[j] selects replica j + 8r's threshold: a per-site table entry (SQA,
 // table mode) or an index in the site's window of the threshold row.
 template <int KIND, bool LUT>
-__device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const Smem &sm, int inst, int w0,
-                                           int wc, int t, int si, int z, int w)
+__device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const Smem &sm, const Part &pt,
+                                           int inst, int w0, int wc, int t, int si, int zl, int w)
 {
     const SiteRec &sr = sm.sites[si];
-    uint32_t *row = sm.S + (size_t)z * J.zstride;
-    const uint32_t s = row[si * wc + w];
-    const int Z = J.Z;
+    uint32_t *row = sm.S + (size_t)zl * J.zstride;
+    const int idx = si * wc + w;
+    const uint32_t s = row[idx];
+    const int z = pt.z0 + zl;  // global slice / slot
     uint32_t code[8];
     {
         uint32_t pl[kMaxTerms], kw[kMaxTerms];
         term_planes(sr, row, wc, w, s, pl, kw);
         uint32_t d1 = 0u, d2 = 0u;
         if (KIND == SQA_KIND_SQA) {
-            const int zu = z == 0 ? Z - 1 : z - 1;
-            const int zd = z == Z - 1 ? 0 : z + 1;
             // temporal disagreements: m = sigma (sigma_up + sigma_dn) = 2 - 2 (d1 + d2)
-            d1 = s ^ sm.S[(size_t)zu * J.zstride + si * wc + w];
-            d2 = s ^ sm.S[(size_t)zd * J.zstride + si * wc + w];
+            if (zl > 0)
+                d1 = s ^ sm.S[(size_t)(zl - 1) * J.zstride + idx];
+            else if (pt.C > 1)
+                d1 = s ^ pt.up[idx];
+            else
+                d1 = s ^ sm.S[(size_t)(pt.zr - 1) * J.zstride + idx];
+            if (zl < pt.zr - 1)
+                d2 = s ^ sm.S[(size_t)(zl + 1) * J.zstride + idx];
+            else if (pt.C > 1)
+                d2 = s ^ pt.dn[idx];
+            else
+                d2 = s ^ sm.S[idx];
         }
         if (KIND == SQA_KIND_SQA && LUT) {
             code[0] = d1;
@@ -236,10 +272,10 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
         }
     }
     const int32_t *Q = (KIND == SQA_KIND_SQA && LUT) ? sm.lut + sr.lut_off
-                       : (KIND == SQA_KIND_SQA ? sm.Tq + sr.base : sm.Tq + (size_t)z * J.nrow + sr.base);
-    const uint32_t *Tfull = KIND == SQA_KIND_SQA ? sm.T : sm.T + (size_t)z * J.nrow;
+                       : (KIND == SQA_KIND_SQA ? sm.Tq + sr.base : sm.Tq + (size_t)zl * J.nrow + sr.base);
+    const uint32_t *Tfull = KIND == SQA_KIND_SQA ? sm.T : sm.T + (size_t)zl * J.nrow;
     const int gw = w0 + w;
-    const uint32_t slot = (uint32_t)(sr.canon * Z + z);
+    const uint32_t slot = (uint32_t)(sr.canon * J.Z + z);
     const uint32_t g0 = (uint32_t)gw * 4u;
     uint32_t acc = 0u;
 #pragma unroll
@@ -281,7 +317,7 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
         }
         acc = (acc << 8) | hi;
     }
-    row[si * wc + w] = s ^ (acc & valid_bits(J.R, gw));
+    row[idx] = s ^ (acc & valid_bits(J.R, gw));
 }
 
 // SQA: per-site tables for sweep t from the staged threshold row: entry c is
@@ -297,19 +333,18 @@ __device__ void build_luts(const JobDev &J, const Smem &sm)
     }
 }
 
-// PT: energies of every (slot, replica) of the unit.  E_b = sum_t w_t -
-// 2 sum_classes w_c n_c(b), where n_c(b) counts the terms of weight class c
-// whose value is negative for replica b.  One thread per (slot, word, class)
-// keeps n_c for all 32 replicas as a bit-sliced counter (plane k = bit k of
-// every replica's count), then adds -2 w_c n_c(b) into E.  Instances with too
-// many distinct weights fall back to a per-replica loop.
-__device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc)
+// PT: energies of the block's slots.  E_b = sum_t w_t - 2 sum_classes w_c
+// n_c(b), where n_c(b) counts the terms of weight class c whose value is
+// negative for replica b.  One thread per (slot, word, class) keeps n_c for
+// all 32 replicas as a bit-sliced counter (plane k = bit k of every
+// replica's count), then adds -2 w_c n_c(b) into E.  Instances with too many
+// distinct weights fall back to a per-replica loop.
+__device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc, int zr)
 {
-    const int P = J.Z;
     const ETerm *et = J.eterms + (size_t)inst * J.n_eterms;
     const int nthr = blockDim.x;
     if (J.n_ecls == 0) {
-        for (int it = threadIdx.x; it < P * wc * 32; it += nthr) {
+        for (int it = threadIdx.x; it < zr * wc * 32; it += nthr) {
             const int b = it & 31, r = it >> 5, w = r % wc, p = r / wc;
             const uint32_t *row = sm.S + (size_t)p * J.zstride;
             int32_t E = 0;
@@ -327,10 +362,10 @@ __device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc)
     }
     const EClass *cls = J.ecls + (size_t)inst * kMaxEClasses;
     const int total = cls[0].total;
-    for (int it = threadIdx.x; it < P * wc * 32; it += nthr) sm.E[it] = total;
+    for (int it = threadIdx.x; it < zr * wc * 32; it += nthr) sm.E[it] = total;
     __syncthreads();
     const int nc = J.n_ecls;
-    for (int it = threadIdx.x; it < P * wc * nc; it += nthr) {
+    for (int it = threadIdx.x; it < zr * wc * nc; it += nthr) {
         const int c = it % nc, r = it / nc, w = r % wc, p = r / wc;
         const EClass k = cls[c];
         if (k.count == 0) continue;
@@ -364,22 +399,35 @@ __device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc)
 }
 
 // PT swap event e: slots (p, p+1) with p = e%2, e%2 + 2, ... exchange
-// configurations replica by replica (Eq. 9).
-__device__ void pt_swap(const JobDev &J, const Smem &sm, int inst, int w0, int wc, int e)
+// configurations replica by replica (Eq. 9).  The block handles the pairs
+// whose lower slot it owns; a pair straddling two blocks reads the upper
+// slot's energies and words from the next block and writes its words there.
+__device__ void pt_swap(const JobDev &J, const Smem &sm, const Part &pt, int inst, int w0, int wc, int e)
 {
-    const int P = J.Z, n = J.n;
+    const int P = J.Z, n = J.n, zr = pt.zr, z0 = pt.z0;
     const int nthr = blockDim.x;
     __syncthreads();
-    pt_energies(J, sm, inst, wc);
-    __syncthreads();
-    const int p0 = e & 1;
-    const int npairs = p0 + 1 < P ? (P - p0) / 2 : 0;
+    pt_energies(J, sm, inst, wc, zr);
+    cluster_barrier(pt.C);  // every block's energies are final
+    const int32_t *E_next = sm.E;
+    uint32_t *S_next = sm.S;
+    if (pt.C > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        const int nr = (pt.rank + 1) % pt.C;
+        E_next = cl.map_shared_rank(sm.E, nr);
+        S_next = cl.map_shared_rank(sm.S, nr);
+    }
+    // pairs with the lower slot in [z0, z0+zr) and the upper slot < P
+    const int first = z0 + ((((e & 1) - z0) % 2) + 2) % 2;
+    const int last = min(z0 + zr - 1, P - 2);
+    const int npairs = last >= first ? (last - first) / 2 + 1 : 0;
     for (int it = threadIdx.x; it < npairs * wc * 32; it += nthr) {
         const int b = it & 31, r = it >> 5, w = r % wc, k = r / wc;
-        const int p = p0 + 2 * k;
+        const int p = first + 2 * k, pl = p - z0;
         const int gw = w0 + w;
         const int rho = gw * 32 + b;
-        const int dE = sm.E[((p + 1) * wc + w) * 32 + b] - sm.E[(p * wc + w) * 32 + b];
+        const int32_t Eu = pl + 1 < zr ? sm.E[((pl + 1) * wc + w) * 32 + b] : E_next[(0 * wc + w) * 32 + b];
+        const int dE = Eu - sm.E[(pl * wc + w) * 32 + b];
         bool accept = dE <= 0;
         if (!accept && dE <= J.sw_len[p]) {
             const U4 v = philox((uint32_t)e, (uint32_t)p, (uint32_t)(rho >> 2), (uint32_t)inst, J.seed_lo,
@@ -392,14 +440,15 @@ __device__ void pt_swap(const JobDev &J, const Smem &sm, int inst, int w0, int w
     __syncthreads();
     for (int it = threadIdx.x; it < npairs * n * wc; it += nthr) {
         const int w = it % wc, r = it / wc, si = r % n, k = r / n;
-        const int p = p0 + 2 * k;
-        uint32_t *a = sm.S + (size_t)p * J.zstride + si * wc + w;
-        uint32_t *c = sm.S + (size_t)(p + 1) * J.zstride + si * wc + w;
-        const uint32_t d = (*a ^ *c) & sm.M[k * wc + w];
-        *a ^= d;
-        *c ^= d;
+        const int pl = first + 2 * k - z0;
+        uint32_t *a = sm.S + (size_t)pl * J.zstride + si * wc + w;
+        uint32_t *c = pl + 1 < zr ? sm.S + (size_t)(pl + 1) * J.zstride + si * wc + w : S_next + si * wc + w;
+        const uint32_t va = *a, vc = *c;
+        const uint32_t d = (va ^ vc) & sm.M[k * wc + w];
+        *a = va ^ d;
+        *c = vc ^ d;
     }
-    __syncthreads();
+    cluster_barrier(pt.C);  // swapped words are visible before the next sweep
 }
 
 template <int KIND, bool LUT>
@@ -408,10 +457,24 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int Z = J.Z, n = J.n, wc = u.wc, inst = u.inst, w0 = u.w0;
     const Keys K{J.seed_lo, J.key_hi, J.key_lo};
-    // stage state and site records
-    for (int i = tid; i < Z * n * wc; i += nthr) {
-        const int w = i % wc, r = i / wc, si = r % n, z = r / n;
-        sm.S[(size_t)z * J.zstride + si * wc + w] = J.state[(((size_t)inst * Z + z) * n + si) * J.W + w0 + w];
+    Part pt;
+    pt.C = J.csize;
+    pt.zr = J.zr;
+    pt.rank = 0;
+    pt.up = pt.dn = nullptr;
+    if (pt.C > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        pt.rank = (int)cl.block_rank();
+        pt.up = cl.map_shared_rank(sm.S, (pt.rank + pt.C - 1) % pt.C) + (size_t)(pt.zr - 1) * J.zstride;
+        pt.dn = cl.map_shared_rank(sm.S, (pt.rank + 1) % pt.C);
+    }
+    pt.z0 = pt.rank * pt.zr;
+    const int zr = pt.zr, z0 = pt.z0;
+    // stage this block's slices and the site records
+    for (int i = tid; i < zr * n * wc; i += nthr) {
+        const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
+        sm.S[(size_t)zl * J.zstride + si * wc + w] =
+            J.state[(((size_t)inst * Z + z0 + zl) * n + si) * J.W + w0 + w];
     }
     {
         const uint32_t *src = (const uint32_t *)(J.sites + (size_t)inst * n);
@@ -419,14 +482,14 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
         for (int i = tid; i < n * (int)(sizeof(SiteRec) / 4); i += nthr) dst[i] = src[i];
     }
     if (KIND == SQA_KIND_PT)
-        for (int i = tid; i < Z * J.nrow; i += nthr) {
-            const uint32_t T = J.T[i];
+        for (int i = tid; i < zr * J.nrow; i += nthr) {
+            const uint32_t T = J.T[(size_t)z0 * J.nrow + i];
             sm.T[i] = T;
             sm.Tq[i] = neg_high(T);
         }
-    __syncthreads();
+    cluster_barrier(pt.C);
     const FastDiv div_w = make_div((uint32_t)wc);
-    const FastDiv div_z = make_div((uint32_t)(KIND == SQA_KIND_SQA ? (Z >> 1) : Z));
+    const FastDiv div_z = make_div((uint32_t)(KIND == SQA_KIND_SQA ? (zr >> 1) : zr));
 
     for (int t = J.t0; t < J.t1; t++) {
         if (KIND == SQA_KIND_SQA) {
@@ -440,7 +503,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 build_luts(J, sm);
                 __syncthreads();
             }
-            const int half = Z >> 1;
+            const int half = zr >> 1;
             for (int cls = 0; cls < 2 * J.ncol; cls++) {
                 const int chi = cls >> 1, par = cls & 1;
                 const int c0 = J.col_ptr[chi];
@@ -448,46 +511,44 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 for (int it = tid; it < nitems; it += nthr) {
                     const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
                     const int q = (int)fdiv((uint32_t)r, div_z), zh = r - q * half;
-                    sweep_item<SQA_KIND_SQA, LUT>(J, K, sm, inst, w0, wc, t, c0 + q, 2 * zh + par, w);
+                    sweep_item<SQA_KIND_SQA, LUT>(J, K, sm, pt, inst, w0, wc, t, c0 + q, 2 * zh + par, w);
                 }
-                __syncthreads();
+                cluster_barrier(pt.C);  // neighbouring blocks read this phase's boundary slices
             }
         } else {
             for (int chi = 0; chi < J.ncol; chi++) {
                 const int c0 = J.col_ptr[chi];
-                const int nitems = (J.col_ptr[chi + 1] - c0) * Z * wc;
+                const int nitems = (J.col_ptr[chi + 1] - c0) * zr * wc;
                 for (int it = tid; it < nitems; it += nthr) {
                     const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
-                    const int q = (int)fdiv((uint32_t)r, div_z), p = r - q * Z;
-                    sweep_item<SQA_KIND_PT, false>(J, K, sm, inst, w0, wc, t, c0 + q, p, w);
+                    const int q = (int)fdiv((uint32_t)r, div_z), p = r - q * zr;
+                    sweep_item<SQA_KIND_PT, false>(J, K, sm, pt, inst, w0, wc, t, c0 + q, p, w);
                 }
                 __syncthreads();
             }
-            if (Z > 1 && (t + 1) % J.swap_every == 0) pt_swap(J, sm, inst, w0, wc, (t + 1) / J.swap_every - 1);
+            if (Z > 1 && (t + 1) % J.swap_every == 0) pt_swap(J, sm, pt, inst, w0, wc, (t + 1) / J.swap_every - 1);
         }
     }
-    for (int i = tid; i < Z * n * wc; i += nthr) {
-        const int w = i % wc, r = i / wc, si = r % n, z = r / n;
-        J.state[(((size_t)inst * Z + z) * n + si) * J.W + w0 + w] = sm.S[(size_t)z * J.zstride + si * wc + w];
+    for (int i = tid; i < zr * n * wc; i += nthr) {
+        const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
+        J.state[(((size_t)inst * Z + z0 + zl) * n + si) * J.W + w0 + w] = sm.S[(size_t)zl * J.zstride + si * wc + w];
     }
+    cluster_barrier(pt.C);  // no block restages while another still reads its slices
 }
 
 // One job: the descriptor is a kernel parameter, so its fields (the Philox
 // keys among them) are uniform across the grid.  One instantiation per path
-// (0 PT, 1 SQA windows, 2 SQA tables) so each gets its own registers.
+// (0 PT, 1 SQA windows, 2 SQA tables) so each gets its own registers.  Units
+// go to clusters in turn (all units of a job cost the same).
 template <int MODE>
 __global__ void __launch_bounds__(256, 3) sweep_kernel_one(const __grid_constant__ JobDev J, const Unit *units,
                                                            int n_units, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_unit;
     const Smem sm = carve(J, smem_raw);
-    for (;;) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
-        __syncthreads();
-        const int ui = s_unit;
-        __syncthreads();
-        if (ui >= n_units) break;
+    const int C = J.csize;
+    const int cid = (int)blockIdx.x / C, ncl = (int)gridDim.x / C;
+    for (int ui = cid; ui < n_units; ui += ncl) {
         const Unit u = units[ui];
         if (MODE == 0)
             run_unit<SQA_KIND_PT, false>(J, sm, u);
@@ -495,22 +556,12 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel_one(const __grid_constant
             run_unit<SQA_KIND_SQA, true>(J, sm, u);
         else
             run_unit<SQA_KIND_SQA, false>(J, sm, u);
-        __syncthreads();
     }
 }
 
 // Host side of the single-job kernel: its entry for a job's path, and the
-// launch.
+// launch (a cluster launch when the job's units span several blocks).
 static int one_mode(const JobDev &J) { return J.kind == SQA_KIND_PT ? 0 : (J.use_lut ? 2 : 1); }
-
-const void *sweep_one_entry(const JobDev &J)
-{
-    switch (one_mode(J)) {
-    case 0: return (const void *)sweep_kernel_one<0>;
-    case 1: return (const void *)sweep_kernel_one<1>;
-    default: return (const void *)sweep_kernel_one<2>;
-    }
-}
 
 const void *sweep_one_entry_mode(int mode)
 {
@@ -518,19 +569,54 @@ const void *sweep_one_entry_mode(int mode)
                      : (mode == 1 ? (const void *)sweep_kernel_one<1> : (const void *)sweep_kernel_one<2>);
 }
 
+const void *sweep_one_entry(const JobDev &J) { return sweep_one_entry_mode(one_mode(J)); }
+
 cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, int *counter, int grid,
                              cudaStream_t s)
 {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = (size_t)J.smem_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)J.csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     switch (one_mode(J)) {
-    case 0: sweep_kernel_one<0><<<grid, 256, J.smem_bytes, s>>>(J, units, n_units, counter); break;
-    case 1: sweep_kernel_one<1><<<grid, 256, J.smem_bytes, s>>>(J, units, n_units, counter); break;
-    default: sweep_kernel_one<2><<<grid, 256, J.smem_bytes, s>>>(J, units, n_units, counter); break;
+    case 0: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<0>, J, units, n_units, counter);
+    case 1: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<1>, J, units, n_units, counter);
+    default: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<2>, J, units, n_units, counter);
     }
-    return cudaGetLastError();
 }
 
-// Several jobs of any shapes: each unit names its job; the block copies that
-// job's descriptor into shared memory.
+// Clusters of C blocks of this job's path that can be resident at once.
+int max_active_clusters(const JobDev &J)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)J.csize * 1024u);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = (size_t)J.smem_bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)J.csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, sweep_one_entry(J), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+// Several jobs of any shapes (each unit in one block): each unit names its
+// job; the block copies that job's descriptor into shared memory.
 __global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const Unit *units, int n_units,
                                                        int *counter)
 {
@@ -544,6 +630,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const
         if (ui < n_units && threadIdx.x == 0) s_job = jobs[units[ui].job];
         __syncthreads();
         if (ui >= n_units) break;
+        if (s_job.csize != 1) continue;  // units of this kernel live in one block
         const Unit u = units[ui];
         const Smem sm = carve(s_job, smem_raw);
         if (s_job.kind == SQA_KIND_PT)

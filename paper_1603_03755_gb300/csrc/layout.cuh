@@ -14,7 +14,7 @@
 namespace sqa {
 
 struct SmemOffsets {
-    size_t S;      // state [Z][zstride] words
+    size_t S;      // state [zr][zstride] words (this block's slices or slots)
     size_t T;      // full thresholds: SQA one row, PT P rows
     size_t Tq;     // negated high halves of the thresholds: PT P rows, SQA window mode one row
     size_t lut;    // SQA: per-site tables of negated high halves
@@ -31,12 +31,12 @@ SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
     SmemOffsets o;
     size_t off = 0;
     o.S = off;
-    off += (size_t)J.Z * zstride * 4;
+    off += (size_t)J.zr * zstride * 4;
     o.T = off;
-    off += (size_t)(J.kind == SQA_KIND_SQA ? J.nrow : J.Z * J.nrow) * 4;
+    off += (size_t)(J.kind == SQA_KIND_SQA ? J.nrow : J.zr * J.nrow) * 4;
     o.Tq = off;
     if (J.kind == SQA_KIND_PT)
-        off += (size_t)J.Z * J.nrow * 4;
+        off += (size_t)J.zr * J.nrow * 4;
     else if (!J.use_lut)
         off += (size_t)J.nrow * 4;
     o.lut = off;
@@ -47,9 +47,9 @@ SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
     o.E = off;
     o.M = off;
     if (J.kind == SQA_KIND_PT) {
-        off += (size_t)J.Z * wc * 32 * 4;
+        off += (size_t)J.zr * wc * 32 * 4;
         o.M = off;
-        off += (size_t)(J.Z / 2 + 1) * wc * 4;
+        off += (size_t)(J.zr / 2 + 1) * wc * 4;
     }
     o.total = align16(off);
     return o;

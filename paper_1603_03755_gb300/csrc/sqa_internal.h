@@ -82,6 +82,8 @@ struct JobDev {
     int lut_entries; // SQA: sum over sites of 2^(nterm+2)
     int use_lut;     // SQA: 1 = per-site code tables, 0 = byte-wise index windows
     int n_ecls;      // weight classes used (max over instances); 0 = too many distinct weights
+    int csize;       // blocks per unit (a thread-block cluster when > 1)
+    int zr;          // slices (SQA) or slots (PT) per block: Z / csize
 };
 
 // One unit of work: the words [w0, w0+wc) of one instance of one job.

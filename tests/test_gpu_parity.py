@@ -250,3 +250,49 @@ def test_launch_shapes_give_the_oracle_bits(emb, use_table, wc):
     for i in range(2):
         pb, q = oracle_sqa(emb, N, J[i], pen, L, R, 3.0, S, 77, i)
         assert np.array_equal(st[i], q.s)
+
+
+@pytest.mark.parametrize("kind,emb,N,Z,R,C", [("sqa", "lhz", 8, 16, 64, 2), ("sqa", "me", 12, 16, 40, 4),
+                                              ("sqa", "lhz", 6, 16, 33, 8), ("pt", "me", 8, 8, 64, 2),
+                                              ("pt", "lhz", 7, 8, 32, 4), ("pt", "me", 5, 16, 40, 8)])
+def test_cluster_split_gives_the_oracle_bits(kind, emb, N, Z, R, C):
+    """A thread-block cluster sweeping one unit, each block holding Z/C slices or
+    slots (temporal neighbours and swap partners across blocks)."""
+    pen = 6 if emb == "me" else 9
+    S = 24
+    J = W.random_instances(N, 2, 500 + C)
+    kw = dict(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=500 + C, kind=kind)
+    if kind == "sqa":
+        kw.update(L=Z, beta=3.0)
+    else:
+        kw.update(betas=W.geometric_ladder(Z, 5.0, 0.2), swap_every=1 if C != 4 else 3)
+    h = pkg.Handle(**kw)
+    h.tune(0, -1, C)
+    assert h.launch()["cluster"] == C
+    h.run(stream=0)
+    st = gpu_state(h)
+    E = h.energies(stream=0)
+    for i in range(2):
+        pb = O.Problem(emb, N, J[i], pen)
+        if kind == "sqa":
+            A, B = O.linear_schedule(S)
+            q = O.SQA(pb, Z, R, 3.0, A, B, 500 + C, i)
+            q.run(0, S)
+            assert np.array_equal(st[i], q.s)
+        else:
+            o = O.PT(pb, kw["betas"], R, kw["swap_every"], 500 + C, i)
+            o.run(0, S)
+            assert np.array_equal(st[i], o.s)
+            assert np.array_equal(E[i], o.E)
+
+
+def test_word_larger_than_one_block_is_split_across_a_cluster():
+    """LHZ K_40 at L = 128: one 32-replica word of state is 400 KB, more than
+    one block's shared memory; the planner splits the slices over a cluster."""
+    N, L, R, S = 40, 128, 32, 3
+    J = W.random_instances(N, 1, 9)
+    h = pkg.Handle(embedding="lhz", N=N, J=J, penalty=9, sweeps=S, R=R, seed=9, L=L, beta=10 / 3)
+    assert h.launch()["cluster"] >= 2
+    h.run(stream=0)
+    pb, q = oracle_sqa("lhz", N, J[0], 9, L, R, 10 / 3, S, 9)
+    assert np.array_equal(gpu_state(h)[0], q.s)

@@ -1,0 +1,88 @@
+"""Serving: continuous batching on the GPU.
+
+Jobs of different shapes (SQA and PT, ME and LHZ, several N, L and replica
+counts) are submitted while others are running, under a memory budget that
+holds only some of them at once.  Every job's final state and energies must
+equal the same job run alone through sqa_run, bit for bit, and agree with the
+oracle on a sampled job.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1603_03755_gb300 as pkg
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    out = []
+    specs = [("sqa", "lhz", 8, 32, 64, 400), ("sqa", "me", 12, 16, 40, 300), ("pt", "me", 8, 0, 64, 250),
+             ("sqa", "lhz", 10, 8, 200, 500), ("pt", "lhz", 7, 0, 33, 300), ("sqa", "me", 5, 4, 7, 900),
+             ("sqa", "lhz", 14, 16, 96, 120), ("pt", "me", 16, 0, 32, 150)]
+    for k, (kind, emb, N, L, R, S) in enumerate(specs):
+        kw = dict(embedding=emb, N=N, J=W.random_instances(N, 2, 300 + k), penalty=6 if emb == "me" else 9,
+                  sweeps=S, R=R, seed=300 + k, kind=kind)
+        if kind == "sqa":
+            kw.update(L=L, beta=10 / 3)
+        else:
+            kw.update(betas=W.geometric_ladder(8, 5.0, 0.2), swap_every=2)
+        out.append(kw)
+    return out
+
+
+def test_served_results_equal_alone_runs():
+    jobs = _jobs()
+    budgets = [pkg.plan_device_bytes(**kw) for kw in jobs]
+    srv = pkg.Server(mem_budget_bytes=int(2.5 * max(budgets)), unit_attempts_per_epoch=2_000_000)
+    ids = []
+    for k, kw in enumerate(jobs):
+        ids.append(srv.submit(**kw))
+        if k == 3:
+            time.sleep(0.05)      # later jobs arrive while the first ones run
+    for jid in ids:
+        srv.wait(jid, timeout=600)
+    stats = srv.stats()
+    assert stats["jobs_done"] == len(jobs) and stats["jobs_failed"] == 0
+    assert stats["max_resident"] >= 2           # jobs shared launches
+    assert stats["max_bytes"] <= int(2.5 * max(budgets))
+    for jid, kw, est in zip(ids, jobs, budgets):
+        info = srv.poll(jid)
+        assert info["state"] == "done"
+        # admission estimate: exact but for the work-unit list, which it
+        # sizes for one unit per 32-replica word (an upper bound)
+        slack = kw["J"].shape[0] * ((kw["R"] + 31) // 32) * 16
+        assert info["device_bytes"] <= est <= info["device_bytes"] + slack
+        assert info["t_submit"] <= info["t_start"] <= info["t_done"]
+        st, en = srv.result(jid)
+        h = pkg.Handle(**kw)
+        h.run(stream=0)
+        assert np.array_equal(st, h.state(stream=0)), kw
+        assert np.array_equal(en, h.energies(stream=0)), kw
+        h.close()
+    # one sampled job against the oracle
+    kw = jobs[5]
+    st, _ = srv.result(ids[5])
+    pb = O.Problem(kw["embedding"], kw["N"], kw["J"][1], kw["penalty"])
+    A, B = O.linear_schedule(kw["sweeps"])
+    q = O.SQA(pb, kw["L"], kw["R"], kw["beta"], A, B, kw["seed"], 1)
+    q.run(0, kw["sweeps"])
+    assert np.array_equal(pkg.unpack_words(st[1], kw["R"]), q.s)
+    for jid in ids:
+        srv.release(jid)
+    srv.close()
+
+
+def test_job_larger_than_budget_fails_cleanly():
+    kw = _jobs()[0]
+    srv = pkg.Server(mem_budget_bytes=1024)
+    jid = srv.submit(**kw)
+    srv.wait(jid, timeout=60)
+    info = srv.poll(jid)
+    assert info["state"] == "failed" and info["status"] == pkg.SQA_ERR_NOMEM
+    with pytest.raises(pkg.SQAError):
+        srv.result(jid)
+    srv.close()
