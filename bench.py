@@ -264,8 +264,8 @@ def serving_workload(pkg, capacity, load, n_jobs=200, seed=0):
             "arrival_rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "p50_queue_s": float(np.percentile(qwait, 50)),
             "attempts_per_s": float(att[np.array(done)].sum() / span), "makespan_s": span,
-            "epochs": st["epochs"], "graphs_built": st["graphs_built"], "max_resident_jobs": st["max_resident"],
-            "worker_s": {"admit": st["admit_s"], "epoch": st["epoch_s"], "retire": st["retire_s"]},
+            "chunks": st["chunks"], "max_resident_jobs": st["max_resident"],
+            "worker_s": {"admit": st["admit_s"], "advance": st["advance_s"], "idle": st["idle_s"]},
             "failed_status": sorted({int(i["status"]) for i in infos if i["state"] != "done"})}
 
 

@@ -199,21 +199,26 @@ typedef struct {
     int64_t device_bytes;  /* device memory the job held while resident */
 } sqa_job_info;
 typedef struct {
-    int64_t jobs_submitted, jobs_done, jobs_failed, epochs, graphs_built, attempts;
+    int64_t jobs_submitted, jobs_done, jobs_failed, chunks, attempts;
     int64_t resident, queued, max_resident, bytes_in_use, max_bytes;
-    double admit_s, epoch_s, retire_s; /* worker wall time in each phase */
+    /* worker wall time: admitting jobs, launching chunks and retiring jobs,
+     * waiting for the GPU */
+    double admit_s, advance_s, idle_s;
     int32_t worker_status, pad_;
 } sqa_server_stats;
 
-/* A server owns a worker thread that serves jobs on the current device.  At
- * each epoch boundary it admits queued jobs in arrival order while their
- * device memory fits mem_budget_bytes (a job larger than the budget fails
- * with SQA_ERR_NOMEM), runs one launch in which every resident job advances
- * its own sweeps (about unit_attempts_per_epoch attempts per block; 0 picks
- * a default), and retires finished jobs (state and energies copied to host,
- * device memory freed).  Results are bit-identical to sqa_run of the same
- * descriptor, whatever else was resident. */
-sqa_status sqa_server_create(int64_t mem_budget_bytes, int64_t unit_attempts_per_epoch, sqa_server **out);
+/* A server owns a worker thread that serves jobs on the current device.  It
+ * admits queued jobs in arrival order while their device memory fits
+ * mem_budget_bytes (a job larger than the budget fails with SQA_ERR_NOMEM),
+ * runs each resident job as a chain of launches ("chunks") of its own sweep
+ * kernel on a stream of its own, about unit_attempts_per_chunk attempts per
+ * work unit each (0 picks a default), so that all resident jobs share the GPU
+ * and none waits for another, and retires finished jobs (state and energies
+ * copied to host, device memory freed in stream order).  Results are
+ * bit-identical to sqa_run of the same descriptor, whatever else was
+ * resident.  The server keeps up to mem_budget_bytes of freed memory in the
+ * device's default stream-ordered memory pool for reuse. */
+sqa_status sqa_server_create(int64_t mem_budget_bytes, int64_t unit_attempts_per_chunk, sqa_server **out);
 /* Copies desc (kind SQA or PT) and queues it; thread-safe. */
 sqa_status sqa_server_submit(sqa_server *s, const sqa_desc *desc, uint64_t *job_id);
 sqa_status sqa_server_poll(sqa_server *s, uint64_t job_id, sqa_job_info *info);
@@ -225,7 +230,7 @@ sqa_status sqa_server_result(sqa_server *s, uint64_t job_id, uint32_t *state_out
 /* Forgets a done or failed job. */
 sqa_status sqa_server_release(sqa_server *s, uint64_t job_id);
 sqa_status sqa_server_get_stats(sqa_server *s, sqa_server_stats *out);
-/* Stops the worker after its current epoch; frees every job. */
+/* Stops the worker, waits for the chunks in flight and frees every job. */
 void sqa_server_destroy(sqa_server *s);
 
 /* ---- host-only views of the library's planning (no device needed) ---- */

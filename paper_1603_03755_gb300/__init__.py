@@ -277,11 +277,10 @@ class _JobInfo(C.Structure):
 
 
 class _ServerStats(C.Structure):
-    _fields_ = [(n, C.c_int64) for n in ("jobs_submitted", "jobs_done", "jobs_failed", "epochs", "graphs_built",
-                                         "attempts", "resident", "queued", "max_resident", "bytes_in_use",
-                                         "max_bytes")] + [("admit_s", C.c_double), ("epoch_s", C.c_double),
-                                                          ("retire_s", C.c_double), ("worker_status", C.c_int32),
-                                                          ("pad_", C.c_int32)]
+    _fields_ = [(n, C.c_int64) for n in ("jobs_submitted", "jobs_done", "jobs_failed", "chunks", "attempts",
+                                         "resident", "queued", "max_resident", "bytes_in_use", "max_bytes")] + \
+               [(n, C.c_double) for n in ("admit_s", "advance_s", "idle_s")] + \
+               [("worker_status", C.c_int32), ("pad_", C.c_int32)]
 
 
 JOB_STATES = ("queued", "running", "done", "failed")
@@ -291,9 +290,9 @@ class Server:
     """Continuous-batching server on the current CUDA device (a worker thread
     in the library).  submit() takes the same keywords as Handle."""
 
-    def __init__(self, mem_budget_bytes: int, unit_attempts_per_epoch: int = 0):
+    def __init__(self, mem_budget_bytes: int, unit_attempts_per_chunk: int = 0):
         s = C.c_void_p()
-        _check(lib().sqa_server_create(int(mem_budget_bytes), int(unit_attempts_per_epoch), C.byref(s)),
+        _check(lib().sqa_server_create(int(mem_budget_bytes), int(unit_attempts_per_chunk), C.byref(s)),
                "sqa_server_create")
         self._s = s
         self._meta = {}

@@ -91,7 +91,8 @@ sqa_status dalloc(sqa_handle *h, T **p, size_t count)
 {
     void *q = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&q, bytes);
+    // stream-ordered: freeing later needs no device-wide synchronization
+    cudaError_t e = cudaMallocAsync(&q, bytes, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         g_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -113,10 +114,10 @@ sqa_status upload(sqa_handle *h, T **p, const std::vector<T> &v)
     return SQA_OK;
 }
 
-void free_all(sqa_handle *h)
+void free_all(sqa_handle *h, cudaStream_t s = 0)
 {
     for (void *p : h->allocs)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, s);
     h->allocs.clear();
     h->device_bytes = 0;
     h->h2d_bytes = 0;
@@ -191,7 +192,10 @@ sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> 
                         const int active = C == 1 ? blocks_per_sm(one_kernel(J), smem) * g_num_sms
                                                   : max_active_clusters(J);
                         const int64_t n_units = (int64_t)h->I * ((J.W + wc - 1) / wc);
-                        const double busy = (double)std::min<int64_t>(n_units, active) * C * (C == 1 ? 1.0 : 0.9);
+                        // PT clusters exchange boundary slots every swap event:
+                        // only when one block cannot hold the unit
+                        const double eff = C == 1 ? 1.0 : (J.kind == SQA_KIND_PT ? 0.05 : 0.9);
+                        const double busy = (double)std::min<int64_t>(n_units, active) * C * eff;
                         const bool better = busy > best.score * 1.0001 ||
                                             (busy >= best.score * 0.9999 && C == best.C &&
                                              (J.use_lut > best.lut || (J.use_lut == best.lut && wc > best.wc)));
@@ -532,7 +536,7 @@ sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
     if (st == SQA_OK) st = launch_init(h, 0);
     if (st == SQA_OK) {
         // the legacy stream: waits for this handle's work only, not for work
-        // on non-blocking streams (a serving loop's running epoch)
+        // on non-blocking streams (the serving loop's chunks in flight)
         cudaError_t e = cudaStreamSynchronize(0);
         if (e != cudaSuccess) st = cuda_fail(e, "sqa_create");
     }
@@ -550,8 +554,24 @@ void sqa_destroy(sqa_handle *h)
     if (!h) return;
     cudaDeviceSynchronize();
     free_all(h);
+    cudaStreamSynchronize(0);
     delete h;
 }
+
+}  // extern "C"
+
+namespace sqa {
+// Frees a handle whose work is known to be complete once stream s reaches
+// this point (the serving loop): no device-wide synchronization.
+void destroy_on_stream(sqa_handle *h, cudaStream_t s)
+{
+    if (!h) return;
+    free_all(h, s);
+    delete h;
+}
+}  // namespace sqa
+
+extern "C" {
 
 sqa_status sqa_get_info(const sqa_handle *h, sqa_info *o)
 {
@@ -594,7 +614,7 @@ sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, in
     }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "sqa_tune");
-    SQA_CUDA(cudaFree(h->d_units));
+    SQA_CUDA(cudaFreeAsync(h->d_units, 0));
     for (auto &p : h->allocs)
         if (p == (void *)h->d_units) p = nullptr;
     h->d_units = nullptr;

@@ -56,5 +56,9 @@ __global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units,
 // Device bytes sqa_create would allocate for desc (host-only estimate, exact
 // for the state and tables).
 int64_t estimate_device_bytes(const sqa_desc *d);
+// Frees h in stream order on s, without a device-wide synchronization.
+void destroy_on_stream(sqa_handle *h, cudaStream_t s);
+// One launch of a job's own sweep kernel over all its units.
+cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s);
 
 }  // namespace sqa

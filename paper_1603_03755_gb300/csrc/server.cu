@@ -1,26 +1,26 @@
 // Serving loop: continuous batching of SQA and PT jobs on one GPU.
 //
 // Jobs are submitted from any host thread.  One worker thread owns the GPU
-// work: at every epoch boundary it admits queued jobs in arrival order while
-// their device memory fits the budget (creating their resident state), runs
-// one launch of the multi-job sweep kernel in which every resident job
-// advances its own range of sweeps, and retires the jobs that reached their
-// last sweep (state and energies copied to host, device memory freed).  A
-// job's random numbers depend only on its own descriptor and sweep indices,
-// so its result is the same whether it ran alone or among other jobs, and
-// however its sweeps were cut into epochs.
+// work.  It admits queued jobs in arrival order while their device memory
+// fits the budget (planning them on the host and uploading their resident
+// state), gives each a stream from a pool, and keeps one chunk of each
+// resident job's sweeps in flight: one launch of the job's own sweep kernel
+// (its own launch shape, a thread-block cluster per unit when planned so)
+// worth about `unit_attempts` attempts per unit.  When a chunk finishes the
+// worker launches the job's next one, so the kernels of all resident jobs
+// share the GPU, a job's blocks go back to the scheduler between chunks, and
+// no job waits for another at a global barrier.  A finished job's state and
+// energies are copied to the host and its memory is freed in stream order.
 //
-// Sweeps per epoch are chosen per job so that each of its units does about the
-// same work, which bounds the epoch length by the work target rather than by
-// the largest job.  Each resident job runs its own sweep kernel (with its own
-// launch shape, a thread-block cluster per unit when planned so), on a pool of
-// streams so the kernels of all resident jobs share the GPU; new jobs are
-// planned and uploaded on the host while the epoch runs.
+// A job's random numbers depend only on its own descriptor and sweep
+// indices, so its result is the same whether it ran alone or among other
+// jobs, and however its sweeps were cut into chunks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdint>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -32,15 +32,13 @@
 
 namespace sqa {
 void set_error(const std::string &msg);
-// One launch of a job's own sweep kernel over all its units (capi.cu).
-cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s);
 }
-
-constexpr int kPoolStreams = 16;
 
 using namespace sqa;
 
 namespace {
+
+constexpr int kPoolStreams = 64;
 
 struct Job {
     uint64_t id = 0;
@@ -49,7 +47,10 @@ struct Job {
     std::vector<double> A, B, betas;
     sqa_job_info info{};
     sqa_handle *h = nullptr;
-    int t_next = 0;                 // next sweep to run
+    int stream = -1;                // index into the stream pool
+    int t_next = 0;                 // first sweep of the chunk in flight
+    int t_chunk_end = 0;            // end of the chunk in flight
+    cudaEvent_t done = nullptr;     // recorded after the chunk in flight
     std::vector<uint32_t> state;    // [I][Z][n_phys][W] once done
     std::vector<int32_t> energies;  // [I][Z][R] once done
 };
@@ -63,7 +64,7 @@ double now_s(std::chrono::steady_clock::time_point t0)
 
 struct sqa_server {
     int64_t budget = 0;
-    int64_t unit_target = 0;  // attempts per unit per epoch
+    int64_t unit_target = 0;  // attempts per unit per chunk
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -75,49 +76,60 @@ struct sqa_server {
     int64_t used = 0;
     sqa_server_stats stats{};
     int device = 0;
-    cudaStream_t stream = nullptr;
-    // epoch launch resources
-    JobDev *h_jobs = nullptr;  // pinned
-    JobDev *d_jobs = nullptr;
-    Unit *d_units = nullptr;
-    int *d_counter = nullptr;
-    int cap_jobs = 0, cap_units = 0;
-    cudaStream_t pool[16] = {};
-    cudaEvent_t ev_start = nullptr, ev_pool[16] = {};
+    cudaStream_t pool[kPoolStreams] = {};
+    int pool_load[kPoolStreams] = {};
     std::thread worker;
     sqa_status worker_status = SQA_OK;
 };
 
 namespace {
 
-sqa_status ensure_capacity(sqa_server *s, int nj, int nu)
+// Marks j failed with status st (caller holds s->mu).
+void fail_job(sqa_server *s, Job *j, sqa_status st)
 {
-    if (nj > s->cap_jobs) {
-        const int cap = std::max(nj, 2 * s->cap_jobs);
-        if (s->h_jobs) cudaFreeHost(s->h_jobs);
-        if (s->d_jobs) cudaFree(s->d_jobs);
-        s->h_jobs = nullptr;
-        s->d_jobs = nullptr;
-        cudaError_t e = cudaMallocHost((void **)&s->h_jobs, sizeof(JobDev) * cap);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_jobs, sizeof(JobDev) * cap);
-        if (e != cudaSuccess) return cuda_fail(e, "server job buffers");
-        s->cap_jobs = cap;
-    }
-    if (nu > s->cap_units) {
-        const int cap = std::max(nu, 2 * s->cap_units);
-        if (s->d_units) cudaFree(s->d_units);
-        s->d_units = nullptr;
-        cudaError_t e = cudaMalloc((void **)&s->d_units, sizeof(Unit) * cap);
-        if (e != cudaSuccess) return cuda_fail(e, "server unit buffer");
-        s->cap_units = cap;
-    }
+    j->info.state = SQA_JOB_FAILED;
+    j->info.status = st;
+    j->info.t_done = now_s(s->t0);
+    s->stats.jobs_failed++;
+    s->cv_done.notify_all();
+}
+
+// Launches the chunk of j's sweeps that starts at j->t_next, on j's stream.
+sqa_status launch_chunk(sqa_server *s, Job *j)
+{
+    sqa_handle *h = j->h;
+    JobDev J = h->job;
+    const int64_t unit_attempts = (int64_t)J.n * J.zr * J.wc * 32;
+    int64_t sweeps = std::max<int64_t>(1, s->unit_target / std::max<int64_t>(unit_attempts, 1));
+    sweeps = std::min<int64_t>(sweeps, h->S - j->t_next);
+    J.t0 = j->t_next;
+    J.t1 = J.t0 + (int)sweeps;
+    cudaStream_t st = s->pool[j->stream];
+    cudaError_t e = launch_job_sweeps(J, h->d_units, h->n_units, h->d_counter, st);
+    if (e == cudaSuccess) e = cudaEventRecord(j->done, st);
+    if (e != cudaSuccess) return cuda_fail(e, "server chunk");
+    j->t_chunk_end = J.t1;
+    s->stats.chunks++;
     return SQA_OK;
 }
 
-// Admit queued jobs in arrival order while they fit the memory budget; the
-// new jobs go to *into (the resident list, or the list that joins it after
-// the running epoch).
-void admit(sqa_server *s, std::vector<Job *> *into)
+// Releases j's device resources in stream order (caller holds s->mu).
+void drop_device(sqa_server *s, Job *j)
+{
+    if (j->h) {
+        s->used -= j->h->device_bytes;
+        destroy_on_stream(j->h, s->pool[j->stream]);
+        j->h = nullptr;
+    }
+    if (j->done) cudaEventDestroy(j->done);
+    j->done = nullptr;
+    if (j->stream >= 0) s->pool_load[j->stream]--;
+    j->stream = -1;
+}
+
+// Admits queued jobs in arrival order while they fit the memory budget and
+// starts their first chunks.
+void admit(sqa_server *s)
 {
     for (;;) {
         Job *j = nullptr;
@@ -128,118 +140,109 @@ void admit(sqa_server *s, std::vector<Job *> *into)
             const int64_t need = estimate_device_bytes(&j->desc);
             if (need > s->budget) {
                 s->queue.pop_front();
-                j->info.state = SQA_JOB_FAILED;
-                j->info.status = SQA_ERR_NOMEM;
-                j->info.t_done = now_s(s->t0);
-                s->stats.jobs_failed++;
-                s->cv_done.notify_all();
+                fail_job(s, j, SQA_ERR_NOMEM);
                 continue;
             }
-            if (s->used + need > s->budget && !(s->active.empty() && into->empty())) return;  // wait for memory
+            if (s->used + need > s->budget && !s->active.empty()) return;  // wait for memory
             s->queue.pop_front();
         }
         sqa_handle *h = nullptr;
-        const sqa_status st = sqa_create(&j->desc, &h);
+        sqa_status st = sqa_create(&j->desc, &h);
+        cudaEvent_t ev = nullptr;
+        if (st == SQA_OK) {
+            const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                sqa_destroy(h);
+                st = cuda_fail(e, "server event");
+            }
+        }
         std::lock_guard<std::mutex> lock(s->mu);
         if (st != SQA_OK) {
-            j->info.state = SQA_JOB_FAILED;
-            j->info.status = st;
-            j->info.t_done = now_s(s->t0);
-            s->stats.jobs_failed++;
-            s->cv_done.notify_all();
+            fail_job(s, j, st);
             continue;
         }
+        int q = 0;
+        for (int k = 1; k < kPoolStreams; k++)
+            if (s->pool_load[k] < s->pool_load[q]) q = k;
+        s->pool_load[q]++;
+        j->stream = q;
         j->h = h;
+        j->done = ev;
         j->t_next = 0;
         j->info.state = SQA_JOB_RUNNING;
         j->info.t_start = now_s(s->t0);
         j->info.device_bytes = h->device_bytes;
         s->used += h->device_bytes;
-        into->push_back(j);
-        s->stats.max_resident = std::max<int64_t>(s->stats.max_resident, (int64_t)(s->active.size() + into->size()));
+        st = launch_chunk(s, j);
+        if (st != SQA_OK) {
+            cudaStreamSynchronize(s->pool[q]);
+            drop_device(s, j);
+            fail_job(s, j, st);
+            continue;
+        }
+        s->active.push_back(j);
+        s->stats.max_resident = std::max<int64_t>(s->stats.max_resident, (int64_t)s->active.size());
         s->stats.max_bytes = std::max(s->stats.max_bytes, s->used);
     }
 }
 
-// Launch one epoch over the resident jobs (asynchronous): each job's own
-// sweep kernel (a cluster launch when its units span several blocks) for its
-// next range of sweeps, the jobs spread over a pool of streams so their
-// kernels run side by side.
-sqa_status epoch(sqa_server *s)
+// Copies a finished job's state and energies to the host and frees its memory.
+void retire(sqa_server *s, Job *j)
 {
-    const int nj = (int)s->active.size();
-    sqa_status st = ensure_capacity(s, nj, 0);
-    if (st != SQA_OK) return st;
-    cudaError_t e = cudaEventRecord(s->ev_start, s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "server epoch start");
-    for (int k = 0; k < nj; k++) {
-        sqa_handle *h = s->active[k]->h;
-        JobDev J = h->job;
-        const int64_t unit_attempts = (int64_t)J.n * J.zr * J.wc * 32;
-        int64_t sweeps = std::max<int64_t>(1, s->unit_target / std::max<int64_t>(unit_attempts, 1));
-        sweeps = std::min<int64_t>(sweeps, h->S - s->active[k]->t_next);
-        J.t0 = s->active[k]->t_next;
-        J.t1 = J.t0 + (int)sweeps;
-        s->h_jobs[k] = J;
-        cudaStream_t ps = s->pool[k % kPoolStreams];
-        e = cudaStreamWaitEvent(ps, s->ev_start, 0);
-        if (e == cudaSuccess) e = launch_job_sweeps(J, h->d_units, h->n_units, h->d_counter, ps);
-        if (e != cudaSuccess) return cuda_fail(e, "server epoch launch");
+    sqa_handle *h = j->h;
+    cudaStream_t st = s->pool[j->stream];
+    j->state.resize((size_t)h->I * h->job.Z * h->job.n_phys * h->job.W);
+    j->energies.resize((size_t)h->I * h->job.Z * h->R);
+    sqa_status rs = sqa_state(h, j->state.data(), 0, st);
+    if (rs == SQA_OK) rs = sqa_energies(h, j->energies.data(), 0, st);
+    std::lock_guard<std::mutex> lock(s->mu);
+    drop_device(s, j);
+    if (rs == SQA_OK) {
+        j->info.state = SQA_JOB_DONE;
+        j->info.status = SQA_OK;
+        j->info.t_done = now_s(s->t0);
+        s->stats.jobs_done++;
+        s->cv_done.notify_all();
+    } else {
+        fail_job(s, j, rs);
     }
-    for (int q = 0; q < std::min(nj, kPoolStreams); q++) {
-        e = cudaEventRecord(s->ev_pool[q], s->pool[q]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_pool[q], 0);
-        if (e != cudaSuccess) return cuda_fail(e, "server epoch join");
-    }
-    return SQA_OK;
 }
 
-// Wait for the epoch launched by epoch() and advance its jobs.
-sqa_status finish_epoch(sqa_server *s)
-{
-    const int nj = (int)s->active.size();
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "server epoch");
-    for (int k = 0; k < nj; k++) {
-        Job *j = s->active[k];
-        const int ran = s->h_jobs[k].t1 - s->h_jobs[k].t0;
-        j->t_next += ran;
-        s->stats.attempts += (int64_t)ran * (int64_t)j->h->plan.n * j->h->job.Z * j->h->R * j->h->I;
-    }
-    s->stats.epochs++;
-    return SQA_OK;
-}
-
-// Copy finished jobs' results to the host and free their device memory.
-sqa_status retire(sqa_server *s)
+// Accounts every chunk that has finished, then launches the job's next chunk
+// or retires the job.
+sqa_status advance(sqa_server *s, bool *progressed)
 {
     std::vector<Job *> keep;
+    keep.reserve(s->active.size());
+    sqa_status status = SQA_OK;
     for (Job *j : s->active) {
-        sqa_handle *h = j->h;
-        if (j->t_next < h->S) {
+        const cudaError_t q = status == SQA_OK ? cudaEventQuery(j->done) : cudaErrorNotReady;
+        if (q == cudaErrorNotReady) {
             keep.push_back(j);
             continue;
         }
-        j->state.resize((size_t)h->I * h->job.Z * h->job.n_phys * h->job.W);
-        j->energies.resize((size_t)h->I * h->job.Z * h->R);
-        sqa_status st = sqa_state(h, j->state.data(), 0, s->stream);
-        if (st == SQA_OK) st = sqa_energies(h, j->energies.data(), 0, s->stream);
-        const int64_t bytes = h->device_bytes;
-        sqa_destroy(h);
-        std::lock_guard<std::mutex> lock(s->mu);
-        j->h = nullptr;
-        s->used -= bytes;
-        j->info.state = st == SQA_OK ? SQA_JOB_DONE : SQA_JOB_FAILED;
-        j->info.status = st;
-        j->info.t_done = now_s(s->t0);
-        if (st == SQA_OK)
-            s->stats.jobs_done++;
-        else
-            s->stats.jobs_failed++;
-        s->cv_done.notify_all();
+        if (q != cudaSuccess) {
+            status = cuda_fail(q, "server chunk");
+            keep.push_back(j);
+            continue;
+        }
+        *progressed = true;
+        sqa_handle *h = j->h;
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->stats.attempts += (int64_t)(j->t_chunk_end - j->t_next) * h->plan.n * h->job.Z * h->R * h->I;
+        }
+        j->t_next = j->t_chunk_end;
+        if (j->t_next < h->S) {
+            status = launch_chunk(s, j);
+            keep.push_back(j);
+        } else {
+            retire(s, j);
+        }
     }
-    s->active = keep;
-    return SQA_OK;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->active.swap(keep);
+    return status;
 }
 
 void worker_loop(sqa_server *s)
@@ -248,43 +251,37 @@ void worker_loop(sqa_server *s)
     for (;;) {
         {
             std::unique_lock<std::mutex> lock(s->mu);
-            s->cv_work.wait_for(lock, std::chrono::milliseconds(20),
-                                [&] { return s->stop || !s->queue.empty() || !s->active.empty(); });
+            if (s->active.empty())
+                s->cv_work.wait_for(lock, std::chrono::milliseconds(20),
+                                    [&] { return s->stop || !s->queue.empty(); });
             if (s->stop) return;
         }
-        std::vector<Job *> incoming;
-        auto c0 = std::chrono::steady_clock::now();
-        admit(s, &s->active);
-        auto c1 = std::chrono::steady_clock::now();
+        const auto c0 = std::chrono::steady_clock::now();
+        admit(s);
+        const auto c1 = std::chrono::steady_clock::now();
+        bool progressed = false;
+        const sqa_status st = advance(s, &progressed);
+        const auto c2 = std::chrono::steady_clock::now();
         s->stats.admit_s += std::chrono::duration<double>(c1 - c0).count();
-        if (s->active.empty()) continue;
-        sqa_status st = epoch(s);
-        // while the GPU runs the epoch: plan and upload the next jobs
-        auto c2 = std::chrono::steady_clock::now();
-        if (st == SQA_OK) admit(s, &incoming);
-        auto c3 = std::chrono::steady_clock::now();
-        if (st == SQA_OK) st = finish_epoch(s);
-        auto c4 = std::chrono::steady_clock::now();
-        if (st == SQA_OK) st = retire(s);
-        auto c5 = std::chrono::steady_clock::now();
-        s->stats.admit_s += std::chrono::duration<double>(c3 - c2).count();
-        s->stats.epoch_s += std::chrono::duration<double>((c2 - c1) + (c4 - c3)).count();
-        s->stats.retire_s += std::chrono::duration<double>(c5 - c4).count();
-        s->active.insert(s->active.end(), incoming.begin(), incoming.end());
+        s->stats.advance_s += std::chrono::duration<double>(c2 - c1).count();
         if (st != SQA_OK) {
+            // a launch or a chunk failed: fail every resident job
+            for (int q = 0; q < kPoolStreams; q++) cudaStreamSynchronize(s->pool[q]);
             std::lock_guard<std::mutex> lock(s->mu);
             s->worker_status = st;
             for (Job *j : s->active) {
-                j->info.state = SQA_JOB_FAILED;
-                j->info.status = st;
-                if (j->h) {
-                    s->used -= j->h->device_bytes;
-                    sqa_destroy(j->h);
-                    j->h = nullptr;
-                }
+                drop_device(s, j);
+                fail_job(s, j, st);
             }
             s->active.clear();
-            s->cv_done.notify_all();
+            continue;
+        }
+        if (!progressed) {
+            // no chunk finished: wait briefly for the GPU or for a new job
+            std::unique_lock<std::mutex> lock(s->mu);
+            s->cv_work.wait_for(lock, std::chrono::microseconds(100),
+                                [&] { return s->stop || !s->queue.empty(); });
+            s->stats.idle_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - c2).count();
         }
     }
 }
@@ -293,27 +290,30 @@ void worker_loop(sqa_server *s)
 
 extern "C" {
 
-sqa_status sqa_server_create(int64_t mem_budget_bytes, int64_t unit_attempts_per_epoch, sqa_server **out)
+sqa_status sqa_server_create(int64_t mem_budget_bytes, int64_t unit_attempts_per_chunk, sqa_server **out)
 {
-    if (!out || mem_budget_bytes <= 0 || unit_attempts_per_epoch < 0) return set_error("server arguments"), SQA_ERR_INVALID;
+    if (!out || mem_budget_bytes <= 0 || unit_attempts_per_chunk < 0) return set_error("server arguments"), SQA_ERR_INVALID;
     *out = nullptr;
     sqa_status st = device_ready();
     if (st != SQA_OK) return st;
     sqa_server *s = new (std::nothrow) sqa_server();
     if (!s) return SQA_ERR_NOMEM;
     s->budget = mem_budget_bytes;
-    s->unit_target = unit_attempts_per_epoch > 0 ? unit_attempts_per_epoch : (int64_t)4e7;
+    s->unit_target = unit_attempts_per_chunk > 0 ? unit_attempts_per_chunk : (int64_t)4e7;
     s->t0 = std::chrono::steady_clock::now();
     cudaGetDevice(&s->device);
-    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&s->d_counter, sizeof(int));
-    for (int q = 0; q < kPoolStreams && e == cudaSuccess; q++) {
-        e = cudaStreamCreateWithFlags(&s->pool[q], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_pool[q], cudaEventDisableTiming);
+    cudaError_t e = cudaSuccess;
+    // keep freed job memory in the device's stream-ordered pool for reuse by
+    // the next jobs instead of handing it back to the driver at each sync
+    cudaMemPool_t mp;
+    if (cudaDeviceGetDefaultMemPool(&mp, s->device) == cudaSuccess) {
+        uint64_t keep = (uint64_t)mem_budget_bytes;
+        cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep);
     }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_start, cudaEventDisableTiming);
+    for (int q = 0; q < kPoolStreams && e == cudaSuccess; q++) e = cudaStreamCreateWithFlags(&s->pool[q], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
-        if (s->stream) cudaStreamDestroy(s->stream);
+        for (int q = 0; q < kPoolStreams; q++)
+            if (s->pool[q]) cudaStreamDestroy(s->pool[q]);
         delete s;
         return cuda_fail(e, "sqa_server_create");
     }
@@ -433,19 +433,16 @@ void sqa_server_destroy(sqa_server *s)
         s->cv_work.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
-    for (Job *j : s->active)
-        if (j->h) sqa_destroy(j->h);
+    for (int q = 0; q < kPoolStreams; q++)
+        if (s->pool[q]) cudaStreamSynchronize(s->pool[q]);
+    for (Job *j : s->active) drop_device(s, j);
+    s->active.clear();
     for (auto &kv : s->jobs) delete kv.second;
-    if (s->h_jobs) cudaFreeHost(s->h_jobs);
-    if (s->d_jobs) cudaFree(s->d_jobs);
-    if (s->d_units) cudaFree(s->d_units);
-    if (s->d_counter) cudaFree(s->d_counter);
-    for (int q = 0; q < kPoolStreams; q++) {
-        if (s->pool[q]) cudaStreamDestroy(s->pool[q]);
-        if (s->ev_pool[q]) cudaEventDestroy(s->ev_pool[q]);
-    }
-    if (s->ev_start) cudaEventDestroy(s->ev_start);
-    if (s->stream) cudaStreamDestroy(s->stream);
+    for (int q = 0; q < kPoolStreams; q++)
+        if (s->pool[q]) {
+            cudaStreamSynchronize(s->pool[q]);
+            cudaStreamDestroy(s->pool[q]);
+        }
     delete s;
 }
 

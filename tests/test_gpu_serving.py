@@ -37,7 +37,7 @@ def _jobs():
 def test_served_results_equal_alone_runs():
     jobs = _jobs()
     budgets = [pkg.plan_device_bytes(**kw) for kw in jobs]
-    srv = pkg.Server(mem_budget_bytes=int(2.5 * max(budgets)), unit_attempts_per_epoch=2_000_000)
+    srv = pkg.Server(mem_budget_bytes=int(2.5 * max(budgets)), unit_attempts_per_chunk=2_000_000)
     ids = []
     for k, kw in enumerate(jobs):
         ids.append(srv.submit(**kw))
