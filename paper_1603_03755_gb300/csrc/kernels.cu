@@ -77,7 +77,7 @@ namespace cg = cooperative_groups;
 struct Smem {
     uint32_t *S;      // [zr][zstride]
     uint32_t *T;      // full thresholds: SQA one row, PT zr rows
-    int32_t *Tq;      // -(T high half << 15): PT zr rows, SQA window mode one row
+    int32_t *Tq;      // T & 0xFFFF0000: PT zr rows, SQA window mode one row
     int32_t *lut;     // SQA table mode: per-site tables by code
     SiteRec *sites;   // [n]
     int32_t *E;       // PT: [zr][wc*32]
@@ -114,10 +114,19 @@ __device__ __forceinline__ void cluster_barrier(int C)
         __syncthreads();
 }
 
-// Negated high half of a threshold, scaled to 31 bits: for a 31-bit value x
-// whose top 16 bits are a uniform's high half h, x + q is negative iff
-// h < T >> 16, and lies in [0, 2^15) iff h == T >> 16 (a tie).
-__device__ __forceinline__ int32_t neg_high(uint32_t T) { return -(int32_t)((T >> 1) & 0x7FFF8000u); }
+// High half of a threshold in place: for a word x whose top 16 bits are a
+// uniform's high half h (any low bits), x >= q iff h >= T >> 16 (reject, but
+// for ties), and x - q lies in [0, 2^16) iff h == T >> 16 (a tie).
+__device__ __forceinline__ int32_t high_part(uint32_t T) { return (int32_t)(T & 0xFFFF0000u); }
+
+// acc = 2 acc + (x >= q): the carry flag of sub.cc (the carry out of
+// x + ~q + 1, set when nothing is borrowed) appended by addc; returns x - q.
+__device__ __forceinline__ uint32_t sub_carry_into(uint32_t x, uint32_t q, uint32_t &acc)
+{
+    uint32_t d;
+    asm("{\n\tsub.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %1, %1;\n\t}" : "=r"(d), "+r"(acc) : "r"(x), "r"(q));
+    return d;
+}
 
 // Term planes of one item: bit b of pl[k] is set when term k's value is
 // negative for replica b (it turns positive on a flip).  kw[k] is K*|w_k|.
@@ -277,7 +286,7 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
     const int gw = w0 + w;
     const uint32_t slot = (uint32_t)(sr.canon * J.Z + z);
     const uint32_t g0 = (uint32_t)gw * 4u;
-    uint32_t acc = 0u;
+    uint32_t rej = 0u;  // bit 8r + j: replica j + 8r rejects
 #pragma unroll
     for (int r = 3; r >= 0; r--) {
         const U4 Ar = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.khi);
@@ -287,11 +296,11 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
         for (int j = 7; j >= 0; j--) {
             const int32_t q = Q[__byte_perm(code[j], 0u, 0x4440u + (uint32_t)r)];
             const uint32_t aw = word_of(Ar, j >> 1);
-            // the replica's 16 high uniform bits at bits 15..30 of x
-            const uint32_t x = (j & 1) ? (aw >> 1) : ((aw & 0xFFFFu) << 15);
-            const uint32_t d = x + (uint32_t)q;
-            hi = __funnelshift_l(d, hi, 1);  // append the sign bit: accepted
-            tie |= d < 0x8000u;
+            // the replica's 16 high uniform bits at the top of x (an odd
+            // replica's low neighbour bits below them do not change x >= q)
+            const uint32_t x = (j & 1) ? aw : (aw << 16);
+            const uint32_t d = sub_carry_into(x, (uint32_t)q, hi);  // append the reject bit
+            tie |= d < 0x10000u;
         }
         if (tie) {
             // high halves equal (probability 2^-16): draw the low half and
@@ -301,27 +310,27 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
             for (int j = 7; j >= 0; j--) {
                 const uint32_t c = __byte_perm(code[j], 0u, 0x4440u + (uint32_t)r);
                 const uint32_t aw = word_of(Ar, j >> 1);
-                const uint32_t x = (j & 1) ? (aw >> 1) : ((aw & 0xFFFFu) << 15);
-                const uint32_t d = x + (uint32_t)Q[c];
-                if (d < 0x8000u) {
+                const uint32_t x = (j & 1) ? aw : (aw << 16);
+                const uint32_t d = x - (uint32_t)Q[c];
+                if (d < 0x10000u) {
                     const uint32_t sh = 16u * (uint32_t)(j & 1);
                     uint32_t u = ((aw >> sh) & 0xFFFFu) << 16 | ((word_of(Br, j >> 1) >> sh) & 0xFFFFu);
                     u = u < 0xFFFFFFFEu ? u : 0xFFFFFFFEu;
                     const uint32_t T = Tfull[LUT ? full_index<KIND>(sr, c) : sr.base + (int)c];
                     if (u < T)
-                        hi |= 1u << j;
-                    else
                         hi &= ~(1u << j);
+                    else
+                        hi |= 1u << j;
                 }
             }
         }
-        acc = (acc << 8) | hi;
+        rej = (rej << 8) | hi;
     }
-    row[idx] = s ^ (acc & valid_bits(J.R, gw));
+    row[idx] = s ^ (~rej & valid_bits(J.R, gw));
 }
 
 // SQA: per-site tables for sweep t from the staged threshold row: entry c is
-// the negated high half of T[base + 2 + sum of K|w_k| over set term bits
+// the high half (T & 0xFFFF0000) of T[base + 2 + sum of K|w_k| over set term bits
 // - the two temporal bits].
 __device__ void build_luts(const JobDev &J, const Smem &sm)
 {
@@ -329,7 +338,7 @@ __device__ void build_luts(const JobDev &J, const Smem &sm)
     for (int si = warp; si < J.n; si += nw) {
         const SiteRec &sr = sm.sites[si];
         const int ne = 1 << (sr.nterm + 2);
-        for (int c = lane; c < ne; c += 32) sm.lut[sr.lut_off + c] = neg_high(sm.T[full_index<SQA_KIND_SQA>(sr, (uint32_t)c)]);
+        for (int c = lane; c < ne; c += 32) sm.lut[sr.lut_off + c] = high_part(sm.T[full_index<SQA_KIND_SQA>(sr, (uint32_t)c)]);
     }
 }
 
@@ -485,7 +494,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
         for (int i = tid; i < zr * J.nrow; i += nthr) {
             const uint32_t T = J.T[(size_t)z0 * J.nrow + i];
             sm.T[i] = T;
-            sm.Tq[i] = neg_high(T);
+            sm.Tq[i] = high_part(T);
         }
     cluster_barrier(pt.C);
     const FastDiv div_w = make_div((uint32_t)wc);
@@ -496,7 +505,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
             for (int i = tid; i < J.nrow; i += nthr) {
                 const uint32_t T = __ldg(J.T + (size_t)t * J.nrow + i);
                 sm.T[i] = T;
-                if (!LUT) sm.Tq[i] = neg_high(T);
+                if (!LUT) sm.Tq[i] = high_part(T);
             }
             __syncthreads();
             if (LUT) {

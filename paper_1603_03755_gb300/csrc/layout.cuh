@@ -16,8 +16,8 @@ namespace sqa {
 struct SmemOffsets {
     size_t S;      // state [zr][zstride] words (this block's slices or slots)
     size_t T;      // full thresholds: SQA one row, PT P rows
-    size_t Tq;     // negated high halves of the thresholds: PT P rows, SQA window mode one row
-    size_t lut;    // SQA: per-site tables of negated high halves
+    size_t Tq;     // high halves of the thresholds (T & 0xFFFF0000): PT P rows, SQA window mode one row
+    size_t lut;    // SQA: per-site tables of threshold high halves
     size_t sites;  // SiteRec [n]
     size_t E;      // PT: energies [P][wc*32]
     size_t M;      // PT: swap masks [P/2+1][wc]
