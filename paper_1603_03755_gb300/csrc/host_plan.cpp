@@ -218,27 +218,31 @@ int build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETer
         out.push_back(e);
     }
     std::stable_sort(out.begin(), out.end(), [](const ETerm &a, const ETerm &b) { return a.w < b.w; });
-    cls.assign(kMaxEClasses, EClass{0, 0, 0, 0});
-    int nc = 0, total = 0;
-    bool too_many = false;
+    // runs of equal weight
+    std::vector<EClass> runs;
+    int total = 0;
     for (size_t q = 0; q < out.size(); q++) {
         total += out[q].w;
-        if (q == 0 || out[q].w != out[q - 1].w) {
-            if (nc == kMaxEClasses) {
-                too_many = true;
-                continue;
-            }
-            cls[nc] = EClass{out[q].w, (int32_t)q, 0, 0};
-            nc++;
-        }
-        if (!too_many) cls[nc - 1].count++;
+        if (q == 0 || out[q].w != out[q - 1].w) runs.push_back(EClass{out[q].w, (int32_t)q, 0, 0});
+        runs.back().count++;
     }
+    cls.assign(kMaxEClasses, EClass{0, 0, 0, 0});
     cls[0].total = total;
-    if (too_many) {
-        for (auto &c : cls) c.count = 0;
-        cls[0].total = total;
-        return 0;
-    }
+    const int nw = (int)runs.size();
+    bool fits = nw <= kMaxEClasses;
+    for (const EClass &r : runs) fits = fits && r.count < 4096;  // 12-plane counters on the device
+    if (!fits) return 0;
+    if (nw == 0) return 0;
+    // cut the runs into pieces of at most `chunk` terms, as many pieces as
+    // the table holds, so that the device's counting threads share the work:
+    // sum ceil(c / chunk) <= n_terms / chunk + nw <= kMaxEClasses
+    const int nt = (int)out.size();
+    const int room = kMaxEClasses - nw;
+    const int chunk = room > 0 ? std::max(16, (nt + room - 1) / room) : nt;
+    int nc = 0;
+    for (const EClass &r : runs)
+        for (int q = 0; q < r.count; q += chunk) cls[nc++] = EClass{r.w, r.start + q, std::min(chunk, r.count - q), 0};
+    cls[0].total = total;
     return nc;
 }
 

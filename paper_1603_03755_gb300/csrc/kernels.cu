@@ -342,12 +342,33 @@ __device__ void build_luts(const JobDev &J, const Smem &sm)
     }
 }
 
-// PT: energies of the block's slots.  E_b = sum_t w_t - 2 sum_classes w_c
-// n_c(b), where n_c(b) counts the terms of weight class c whose value is
-// negative for replica b.  One thread per (slot, word, class) keeps n_c for
-// all 32 replicas as a bit-sliced counter (plane k = bit k of every
-// replica's count), then adds -2 w_c n_c(b) into E.  Instances with too many
-// distinct weights fall back to a per-replica loop.
+// Carry-save adder on bit vectors: a + b + c = l + 2 h in every bit position.
+__device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c)
+{
+    const uint32_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+// Value bits of energy term q for the 32 replicas of word w of a slot's row:
+// bit b set when the product of the term's spins is -1 for replica b.
+__device__ __forceinline__ uint32_t eterm_bits(const ETerm &x, const uint32_t *row, int wc, int w)
+{
+    uint32_t v = row[x.m[0] * wc + w];
+    if (x.size > 1) v ^= row[x.m[1] * wc + w];
+    if (x.size > 2) v ^= row[x.m[2] * wc + w];
+    if (x.size > 3) v ^= row[x.m[3] * wc + w];
+    return v;
+}
+
+// PT: energies of the block's slots.  E_b = sum_t w_t - 2 sum_c w_c n_c(b),
+// where n_c(b) counts the terms of class c (a run of terms of one weight)
+// whose value is negative for replica b.  One thread per (slot, word, class)
+// counts for all 32 replicas at once in bit-sliced form: a carry-save adder
+// tree folds 16 terms into ones/twos/fours/eights planes and a ripple adder
+// takes the sixteens (12 planes, counts below 4096).  Two 8x8 bit-matrix
+// transposes turn the planes into per-replica counts, added into E.
+// Instances with too many distinct weights fall back to a per-replica loop.
 __device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc, int zr)
 {
     const ETerm *et = J.eterms + (size_t)inst * J.n_eterms;
@@ -359,11 +380,7 @@ __device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc, i
             int32_t E = 0;
             for (int q = 0; q < J.n_eterms; q++) {
                 const ETerm x = et[q];
-                uint32_t v = row[x.m[0] * wc + w];
-                if (x.size > 1) v ^= row[x.m[1] * wc + w];
-                if (x.size > 2) v ^= row[x.m[2] * wc + w];
-                if (x.size > 3) v ^= row[x.m[3] * wc + w];
-                E += ((v >> b) & 1u) ? -x.w : x.w;
+                E += ((eterm_bits(x, row, wc, w) >> b) & 1u) ? -x.w : x.w;
             }
             sm.E[(p * wc + w) * 32 + b] = E;
         }
@@ -375,35 +392,62 @@ __device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc, i
     __syncthreads();
     const int nc = J.n_ecls;
     for (int it = threadIdx.x; it < zr * wc * nc; it += nthr) {
-        const int c = it % nc, r = it / nc, w = r % wc, p = r / wc;
+        // consecutive threads take consecutive slots (distinct banks)
+        const int p = it % zr, r = it / zr, w = r % wc, c = r / wc;
         const EClass k = cls[c];
         if (k.count == 0) continue;
         const uint32_t *row = sm.S + (size_t)p * J.zstride;
-        uint32_t cnt[12];
+        uint32_t ones = 0u, twos = 0u, fours = 0u, eights = 0u;
+        uint32_t hi[8];
 #pragma unroll
-        for (int q = 0; q < 12; q++) cnt[q] = 0u;
-        for (int q = k.start; q < k.start + k.count; q++) {
-            const ETerm x = et[q];
-            uint32_t v = row[x.m[0] * wc + w];
-            if (x.size > 1) v ^= row[x.m[1] * wc + w];
-            if (x.size > 2) v ^= row[x.m[2] * wc + w];
-            if (x.size > 3) v ^= row[x.m[3] * wc + w];
-            // add the bit vector v to the bit-sliced counter
+        for (int q2 = 0; q2 < 8; q2++) hi[q2] = 0u;
+        const int q1 = k.start + k.count;
+        for (int q = k.start; q < q1; q += 16) {
+            uint32_t v[16];
 #pragma unroll
-            for (int q2 = 0; q2 < 12; q2++) {
-                const uint32_t carry = cnt[q2] & v;
-                cnt[q2] ^= v;
-                v = carry;
+            for (int i = 0; i < 16; i++) v[i] = q + i < q1 ? eterm_bits(et[q + i], row, wc, w) : 0u;
+            uint32_t tA, tB, fA, fB, eA, eB, s16;
+            csa(tA, ones, ones, v[0], v[1]);
+            csa(tB, ones, ones, v[2], v[3]);
+            csa(fA, twos, twos, tA, tB);
+            csa(tA, ones, ones, v[4], v[5]);
+            csa(tB, ones, ones, v[6], v[7]);
+            csa(fB, twos, twos, tA, tB);
+            csa(eA, fours, fours, fA, fB);
+            csa(tA, ones, ones, v[8], v[9]);
+            csa(tB, ones, ones, v[10], v[11]);
+            csa(fA, twos, twos, tA, tB);
+            csa(tA, ones, ones, v[12], v[13]);
+            csa(tB, ones, ones, v[14], v[15]);
+            csa(fB, twos, twos, tA, tB);
+            csa(eB, fours, fours, fA, fB);
+            csa(s16, eights, eights, eA, eB);
+#pragma unroll
+            for (int q2 = 0; q2 < 8; q2++) {
+                const uint32_t carry = hi[q2] & s16;
+                hi[q2] ^= s16;
+                s16 = carry;
             }
         }
+        // planes -> per-replica counts: byte b of lo[j] / hi[j] holds bits
+        // 0-7 / 8-11 of the count of replica 8b + j
+        uint32_t lo[8] = {ones, twos, fours, eights, hi[0], hi[1], hi[2], hi[3]};
+        uint32_t up[8] = {hi[4], hi[5], hi[6], hi[7], 0u, 0u, 0u, 0u};
+        transpose8(lo);
+        transpose8(up);
         int32_t *Ew = sm.E + (p * wc + w) * 32;
         const int m2w = -2 * k.w;
-        for (int b = 0; b < 32; b++) {
-            int n = 0;
 #pragma unroll
-            for (int q2 = 0; q2 < 12; q2++) n |= (int)((cnt[q2] >> b) & 1u) << q2;
-            if (n) atomicAdd(Ew + b, m2w * n);
-        }
+        for (int j = 0; j < 8; j++)
+#pragma unroll
+            for (int b8 = 0; b8 < 4; b8++) {
+                // start at a slot-dependent replica so that lanes of a warp
+                // hit distinct banks
+                const int bb = (b8 + (p >> 3)) & 3;
+                const int n = (int)(__byte_perm(lo[j], 0u, 0x4440u + (uint32_t)bb) |
+                                    (__byte_perm(up[j], 0u, 0x4440u + (uint32_t)bb) << 8));
+                if (n) atomicAdd(Ew + 8 * bb + j, m2w * n);
+            }
     }
 }
 

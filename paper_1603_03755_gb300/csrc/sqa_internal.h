@@ -39,8 +39,9 @@ struct ETerm {
     int32_t size;
 };
 
-// Energy terms of one instance are sorted by weight; a class is a run of
-// terms with one weight.  Up to kMaxEClasses classes per instance.
+// Energy terms of one instance are sorted by weight; a class is a piece of a
+// run of terms with one weight (runs are cut so that the device's counting
+// threads share the work).  Up to kMaxEClasses classes per instance.
 constexpr int kMaxEClasses = 16;
 struct EClass {
     int32_t w;
@@ -133,7 +134,8 @@ void build_sites(const Plan &pl, const int32_t *J, int penalty, int K, int smax_
                  std::vector<SiteRec> &sites_out);
 int site_weight_sum_max(const Plan &pl, const int32_t *J, int penalty);
 // Energy terms sorted by weight and their classes; returns the number of
-// classes, or 0 when the instance has more than kMaxEClasses distinct weights.
+// classes, or 0 when the instance has more than kMaxEClasses distinct weights
+// or 4096 or more terms of one weight.
 int build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETerm> &out,
                  std::vector<EClass> &cls);
 
