@@ -217,16 +217,18 @@ int build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETer
         e.size = t.size;
         out.push_back(e);
     }
-    std::stable_sort(out.begin(), out.end(), [](const ETerm &a, const ETerm &b) { return a.w < b.w; });
-    // runs of equal weight
+    std::stable_sort(out.begin(), out.end(),
+                     [](const ETerm &a, const ETerm &b) { return a.w != b.w ? a.w < b.w : a.size < b.size; });
+    // runs of equal weight and size
     std::vector<EClass> runs;
     int total = 0;
     for (size_t q = 0; q < out.size(); q++) {
         total += out[q].w;
-        if (q == 0 || out[q].w != out[q - 1].w) runs.push_back(EClass{out[q].w, (int32_t)q, 0, 0});
+        if (q == 0 || out[q].w != out[q - 1].w || out[q].size != out[q - 1].size)
+            runs.push_back(EClass{out[q].w, (int32_t)q, 0, out[q].size, 0, 0});
         runs.back().count++;
     }
-    cls.assign(kMaxEClasses, EClass{0, 0, 0, 0});
+    cls.assign(kMaxEClasses, EClass{0, 0, 0, 0, 0, 0});
     cls[0].total = total;
     const int nw = (int)runs.size();
     bool fits = nw <= kMaxEClasses;
@@ -241,7 +243,7 @@ int build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETer
     const int chunk = room > 0 ? std::max(16, (nt + room - 1) / room) : nt;
     int nc = 0;
     for (const EClass &r : runs)
-        for (int q = 0; q < r.count; q += chunk) cls[nc++] = EClass{r.w, r.start + q, std::min(chunk, r.count - q), 0};
+        for (int q = 0; q < r.count; q += chunk) cls[nc++] = EClass{r.w, r.start + q, std::min(chunk, r.count - q), r.size, 0, 0};
     cls[0].total = total;
     return nc;
 }

@@ -361,13 +361,67 @@ __device__ __forceinline__ uint32_t eterm_bits(const ETerm &x, const uint32_t *r
     return v;
 }
 
+// Bit-sliced count, for each of the 32 replicas, of the n terms (all of SZ
+// spins) at et whose value is negative: P[k] = bit k of every replica's
+// count.  A carry-save adder tree folds 16 terms into ones/twos/fours/eights
+// planes; a ripple adder takes the sixteens (12 planes, counts below 4096).
+// A term's spin indices are read as one 8-byte load.
+template <int SZ>
+__device__ __forceinline__ void count_terms(const ETerm *et, int n, const uint32_t *row, int wc, int w,
+                                            uint32_t (&P)[12])
+{
+    uint32_t ones = 0u, twos = 0u, fours = 0u, eights = 0u;
+#pragma unroll
+    for (int q2 = 4; q2 < 12; q2++) P[q2] = 0u;
+    for (int q = 0; q < n; q += 16) {
+        uint32_t v[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            v[i] = 0u;
+            if (q + i < n) {
+                const uint2 mm = __ldg(reinterpret_cast<const uint2 *>(et + q + i));
+                uint32_t x = row[(int)(mm.x & 0xFFFFu) * wc + w];
+                if (SZ > 1) x ^= row[(int)(mm.x >> 16) * wc + w];
+                if (SZ > 2) x ^= row[(int)(mm.y & 0xFFFFu) * wc + w];
+                if (SZ > 3) x ^= row[(int)(mm.y >> 16) * wc + w];
+                v[i] = x;
+            }
+        }
+        uint32_t tA, tB, fA, fB, eA, eB, s16;
+        csa(tA, ones, ones, v[0], v[1]);
+        csa(tB, ones, ones, v[2], v[3]);
+        csa(fA, twos, twos, tA, tB);
+        csa(tA, ones, ones, v[4], v[5]);
+        csa(tB, ones, ones, v[6], v[7]);
+        csa(fB, twos, twos, tA, tB);
+        csa(eA, fours, fours, fA, fB);
+        csa(tA, ones, ones, v[8], v[9]);
+        csa(tB, ones, ones, v[10], v[11]);
+        csa(fA, twos, twos, tA, tB);
+        csa(tA, ones, ones, v[12], v[13]);
+        csa(tB, ones, ones, v[14], v[15]);
+        csa(fB, twos, twos, tA, tB);
+        csa(eB, fours, fours, fA, fB);
+        csa(s16, eights, eights, eA, eB);
+#pragma unroll
+        for (int q2 = 4; q2 < 12; q2++) {
+            const uint32_t carry = P[q2] & s16;
+            P[q2] ^= s16;
+            s16 = carry;
+        }
+    }
+    P[0] = ones;
+    P[1] = twos;
+    P[2] = fours;
+    P[3] = eights;
+}
+
 // PT: energies of the block's slots.  E_b = sum_t w_t - 2 sum_c w_c n_c(b),
 // where n_c(b) counts the terms of class c (a run of terms of one weight)
 // whose value is negative for replica b.  One thread per (slot, word, class)
-// counts for all 32 replicas at once in bit-sliced form: a carry-save adder
-// tree folds 16 terms into ones/twos/fours/eights planes and a ripple adder
-// takes the sixteens (12 planes, counts below 4096).  Two 8x8 bit-matrix
-// transposes turn the planes into per-replica counts, added into E.
+// counts for all 32 replicas at once in bit-sliced form (count_terms); two
+// 8x8 bit-matrix transposes turn the planes into per-replica counts, added
+// into E.
 // Instances with too many distinct weights fall back to a per-replica loop.
 __device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc, int zr)
 {
@@ -397,42 +451,17 @@ __device__ void pt_energies(const JobDev &J, const Smem &sm, int inst, int wc, i
         const EClass k = cls[c];
         if (k.count == 0) continue;
         const uint32_t *row = sm.S + (size_t)p * J.zstride;
-        uint32_t ones = 0u, twos = 0u, fours = 0u, eights = 0u;
-        uint32_t hi[8];
-#pragma unroll
-        for (int q2 = 0; q2 < 8; q2++) hi[q2] = 0u;
-        const int q1 = k.start + k.count;
-        for (int q = k.start; q < q1; q += 16) {
-            uint32_t v[16];
-#pragma unroll
-            for (int i = 0; i < 16; i++) v[i] = q + i < q1 ? eterm_bits(et[q + i], row, wc, w) : 0u;
-            uint32_t tA, tB, fA, fB, eA, eB, s16;
-            csa(tA, ones, ones, v[0], v[1]);
-            csa(tB, ones, ones, v[2], v[3]);
-            csa(fA, twos, twos, tA, tB);
-            csa(tA, ones, ones, v[4], v[5]);
-            csa(tB, ones, ones, v[6], v[7]);
-            csa(fB, twos, twos, tA, tB);
-            csa(eA, fours, fours, fA, fB);
-            csa(tA, ones, ones, v[8], v[9]);
-            csa(tB, ones, ones, v[10], v[11]);
-            csa(fA, twos, twos, tA, tB);
-            csa(tA, ones, ones, v[12], v[13]);
-            csa(tB, ones, ones, v[14], v[15]);
-            csa(fB, twos, twos, tA, tB);
-            csa(eB, fours, fours, fA, fB);
-            csa(s16, eights, eights, eA, eB);
-#pragma unroll
-            for (int q2 = 0; q2 < 8; q2++) {
-                const uint32_t carry = hi[q2] & s16;
-                hi[q2] ^= s16;
-                s16 = carry;
-            }
+        uint32_t P[12];
+        switch (k.size) {
+        case 1: count_terms<1>(et + k.start, k.count, row, wc, w, P); break;
+        case 2: count_terms<2>(et + k.start, k.count, row, wc, w, P); break;
+        case 3: count_terms<3>(et + k.start, k.count, row, wc, w, P); break;
+        default: count_terms<4>(et + k.start, k.count, row, wc, w, P); break;
         }
-        // planes -> per-replica counts: byte b of lo[j] / hi[j] holds bits
+        // planes -> per-replica counts: byte b of lo[j] / up[j] holds bits
         // 0-7 / 8-11 of the count of replica 8b + j
-        uint32_t lo[8] = {ones, twos, fours, eights, hi[0], hi[1], hi[2], hi[3]};
-        uint32_t up[8] = {hi[4], hi[5], hi[6], hi[7], 0u, 0u, 0u, 0u};
+        uint32_t lo[8] = {P[0], P[1], P[2], P[3], P[4], P[5], P[6], P[7]};
+        uint32_t up[8] = {P[8], P[9], P[10], P[11], 0u, 0u, 0u, 0u};
         transpose8(lo);
         transpose8(up);
         int32_t *Ew = sm.E + (p * wc + w) * 32;

@@ -39,15 +39,18 @@ struct ETerm {
     int32_t size;
 };
 
-// Energy terms of one instance are sorted by weight; a class is a piece of a
-// run of terms with one weight (runs are cut so that the device's counting
-// threads share the work).  Up to kMaxEClasses classes per instance.
+// Energy terms of one instance are sorted by weight and size; a class is a
+// piece of a run of terms with one weight and one size (runs are cut so that
+// the device's counting threads share the work).  Up to kMaxEClasses classes
+// per instance.
 constexpr int kMaxEClasses = 16;
 struct EClass {
     int32_t w;
     int32_t start;
     int32_t count;
+    int32_t size;   // spins per term
     int32_t total;  // class 0 only: sum of every term's weight (E of the all-up state)
+    int32_t pad_;
 };
 
 // Device-side description of one job (one handle) for one launch.
@@ -72,7 +75,7 @@ struct JobDev {
     uint32_t *state;     // [I][Z][n][W]
     const SiteRec *sites;    // [I][n]
     const uint32_t *T;       // SQA [S][nrow]; PT [P][nrow]
-    const ETerm *eterms;     // [I][n_eterms], sorted by weight
+    const ETerm *eterms;     // [I][n_eterms], sorted by weight and size
     const EClass *ecls;      // [I][kMaxEClasses]; count 0 pads
     const uint32_t *Tsw;     // PT swap thresholds, dE = 1..sw_len[p]
     const int *sw_off;       // [P-1]
@@ -133,7 +136,7 @@ bool build_plan(int emb, int N, Plan &out, std::string &err);
 void build_sites(const Plan &pl, const int32_t *J, int penalty, int K, int smax_all,
                  std::vector<SiteRec> &sites_out);
 int site_weight_sum_max(const Plan &pl, const int32_t *J, int penalty);
-// Energy terms sorted by weight and their classes; returns the number of
+// Energy terms sorted by weight and size, and their classes; returns the number of
 // classes, or 0 when the instance has more than kMaxEClasses distinct weights
 // or 4096 or more terms of one weight.
 int build_eterms(const Plan &pl, const int32_t *J, int penalty, std::vector<ETerm> &out,
