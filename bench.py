@@ -57,9 +57,28 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged-batch and PT workloads")
     ap.add_argument("--pt-sweeps", type=int, default=100_000)
     ap.add_argument("--ragged-sweeps", type=int, default=10_000)
+    ap.add_argument("--pt-instances", type=int, default=256)
+    ap.add_argument("--pt-only", choices=["me", "lhz"],
+                    help="time only the PT workload on this embedding (a small case for profiling)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-jobs", type=int, default=200)
     return ap.parse_args()
+
+
+def kernel_traffic(n_instances):
+    """DRAM bytes of one sweep launch from the committed ncu capture of the
+    sweep kernel (read + write, per instance, scaled to n_instances), or None
+    when kernels.cu changed since that capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_1603_03755_gb300", "csrc", "kernels.cu")
+    if not os.path.exists(p):
+        return None, "no capture"
+    rec = json.load(open(p))
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if rec.get("kernels_cu_sha256") != sha:
+        return None, "kernel changed since the capture"
+    return rec["dram_bytes_per_instance"] * n_instances, rec["note"]
 
 
 def load_peaks():
@@ -201,8 +220,18 @@ def extra_workloads(pkg, stream, args):
                          "value": att / t, "unit": UNIT, "seconds": t}
     for h in hs:
         h.close()
-    for emb in ("me", "lhz"):
-        c = W.pt_config(emb, sweeps=args.pt_sweeps)
+    out.update(pt_workloads(pkg, stream, args, ("me", "lhz")))
+    if not args.no_serving:
+        out["serving"] = [serving_workload(pkg, args.capacity, load, args.serving_jobs) for load in (0.5, 0.8, 0.95)]
+    return out
+
+
+def pt_workloads(pkg, stream, args, embs):
+    """PT on ME K_32 / LHZ K_24: 32 temperatures, swap every sweep, R = 32."""
+    sp = stream.cuda_stream
+    out = {}
+    for emb in embs:
+        c = W.pt_config(emb, n_inst=args.pt_instances, sweeps=args.pt_sweeps)
         kw = dict(embedding=emb, N=c["N"], J=c["J"], penalty=c["penalty"], R=c["R"], seed=c["seed"], kind="pt",
                   betas=c["betas"], swap_every=c["swap_every"])
         w = pkg.Handle(sweeps=50, **kw)
@@ -215,8 +244,6 @@ def extra_workloads(pkg, stream, args):
         out[f"pt_{emb}"] = {"workload": c["name"] + f", 32 temperatures, {args.pt_sweeps} sweeps, swap every sweep",
                             "value": att / t, "unit": UNIT, "seconds": t, "launch": h.launch()}
         h.close()
-    if not args.no_serving:
-        out["serving"] = [serving_workload(pkg, args.capacity, load, args.serving_jobs) for load in (0.5, 0.8)]
     return out
 
 
@@ -236,7 +263,7 @@ def serving_workload(pkg, capacity, load, n_jobs=200, seed=0):
     rate = load * capacity / att.mean()                 # jobs per second
     gaps = np.random.default_rng(seed).exponential(1.0 / rate, n_jobs)
     srv = pkg.Server(64 << 30)
-    ids = []
+    ids, kws = [], []
     t0 = time.perf_counter()
     t_next = 0.0
     for j, gap in zip(jobs, gaps):
@@ -250,11 +277,22 @@ def serving_workload(pkg, capacity, load, n_jobs=200, seed=0):
         else:
             kw.update(betas=j["betas"], swap_every=j["swap_every"])
         ids.append(srv.submit(**kw))
+        kws.append(kw)
     infos = []
     for jid in ids:
         srv.wait(jid, timeout=900)
         infos.append(srv.poll(jid))
     st = srv.stats()
+    # the three cheapest jobs again, each alone through sqa_run: same bits
+    alone_equal = []
+    for k in np.argsort(att)[:3]:
+        if infos[k]["state"] != "done":
+            continue
+        got, _ = srv.result(ids[k])
+        h = pkg.Handle(**kws[k])
+        h.run(stream=0)
+        alone_equal.append(bool(np.array_equal(got, h.state(stream=0))))
+        h.close()
     srv.close()
     lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
     qwait = np.array([i["t_start"] - i["t_submit"] for i in infos])
@@ -266,7 +304,8 @@ def serving_workload(pkg, capacity, load, n_jobs=200, seed=0):
             "attempts_per_s": float(att[np.array(done)].sum() / span), "makespan_s": span,
             "chunks": st["chunks"], "max_resident_jobs": st["max_resident"],
             "worker_s": {"admit": st["admit_s"], "advance": st["advance_s"], "idle": st["idle_s"]},
-            "failed_status": sorted({int(i["status"]) for i in infos if i["state"] != "done"})}
+            "failed_status": sorted({int(i["status"]) for i in infos if i["state"] != "done"}),
+            "alone_vs_served_same_bits": alone_equal}
 
 
 def run_reference(args, cfg, world, rank, dist):
@@ -319,6 +358,11 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
+    if args.pt_only:
+        res = pt_workloads(pkg, stream, args, (args.pt_only,))
+        if rank == 0:
+            print(json.dumps({"pt_only": res}))
+        return
     N, R, L, S, I = cfg["N"], cfg["R"], cfg["L"], cfg["sweeps"], cfg["J"].shape[0]
     h = pkg.Handle(embedding="me", N=N, J=cfg["J"], penalty=cfg["penalty"], sweeps=S, R=R,
                    seed=cfg["seed"], L=L, beta=cfg["beta"])
@@ -428,6 +472,7 @@ def main():
     intpeak = {k: round(pkg.int_peak(k), 2) for k in pkg.INT_PEAK_KINDS}
     t_sweep = statistics.mean(sweep_times)
     achieved_gops = attempts * OPS_PER_ATTEMPT / t_sweep / 1e9
+    traffic, traffic_note = kernel_traffic(I)
     args.capacity = value / world
     extra = None if args.no_extra else extra_workloads(pkg, stream, args)
     cpu = None
@@ -442,7 +487,7 @@ def main():
                    "replicas": R, "slices": L, "sweeps": S, "parallelism": "replicas",
                    "l2": "flushed between steps (256 MiB write)"},
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved_gops / peak_gops, "traffic": None,
+                     "frac": achieved_gops / peak_gops, "traffic": traffic, "traffic_note": traffic_note,
                      "kernel": "sweep_kernel", "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_basis": f"{n_sm} SMs x 4 SMSP x 32 lanes x {f_mhz:.0f} MHz (median SM clock under load)",
                      "sweep_kernel_s": t_sweep,
