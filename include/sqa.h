@@ -188,6 +188,36 @@ sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, i
 sqa_status sqa_ground_energy_noalloc(int32_t N, int32_t n_instances, const int32_t *J_dev,
                                      int64_t *e_dev, void *stream);
 
+/* ---- reusable batches (CUDA graph) and the launch-shape autotuner ---- */
+
+typedef struct sqa_batch sqa_batch;
+/* Plans the handles (SQA or PT, any sizes) once for one persistent launch of
+ * the multi-job sweep kernel: every job's units in one list, longest first.
+ * The handles must outlive the batch and must not be tuned or destroyed
+ * while it exists. */
+sqa_status sqa_batch_create(sqa_handle *const *hs, int32_t n, sqa_batch **out);
+/* Asynchronous on stream: fresh initial spins for every job, then all their
+ * sweeps.  The first call captures this sequence into a CUDA graph; every
+ * call replays the graph (the same anneal, bit for bit, as sqa_batch_run). */
+sqa_status sqa_batch_launch(sqa_batch *b, void *stream);
+/* Times the batch with 0 (the planner's words per unit for each job) and
+ * 1, 2, 4, ... words per unit for every job (each job takes the largest of
+ * W, ceil(W/2), ... not above it), n_trial sweeps each, and keeps the
+ * fastest.  Synchronous; leaves the handles' spins at the end of a trial (a
+ * launch starts from fresh initial spins).  words_per_unit and
+ * attempts_per_s (either may be NULL) receive the choice and its trial
+ * rate. */
+sqa_status sqa_batch_autotune(sqa_batch *b, int32_t n_trial, void *stream, int32_t *words_per_unit,
+                              double *attempts_per_s);
+void sqa_batch_destroy(sqa_batch *b);
+/* Times h's sweep kernel in every launch shape that fits (cluster size 1, 2,
+ * 4, 8; table or window lookup; words per unit W, ceil(W/2), ..., 1) on
+ * n_trial sweeps from sweep 0 and keeps the fastest (as sqa_tune).  h's
+ * spins are saved and restored.  Synchronous; the out pointers (may be
+ * NULL) receive the choice and its trial rate in attempts/s. */
+sqa_status sqa_autotune(sqa_handle *h, int32_t n_trial, void *stream, int32_t *words_per_unit,
+                        int32_t *use_table, int32_t *cluster, double *attempts_per_s);
+
 /* ---- serving: continuous batching of SQA and PT jobs ---- */
 
 typedef struct sqa_server sqa_server;

@@ -61,6 +61,13 @@ _SIGS = {
     "sqa_run_per_instance": (C.c_int, [C.c_void_p, C.c_void_p]),
     "pt_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "sqa_batch_run": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)]),
+    "sqa_batch_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sqa_batch_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double)]),
+    "sqa_batch_destroy": (None, [C.c_void_p]),
+    "sqa_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "sqa_readout": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sqa_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sqa_energies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
@@ -200,6 +207,15 @@ class Handle:
     # ---- launch shape ----
     def tune(self, words_per_unit: int = 0, use_table: int = -1, cluster: int = 0):
         _check(lib().sqa_tune(self._h, words_per_unit, use_table, cluster), "sqa_tune")
+
+    def autotune(self, n_trial: int = 20, stream=None) -> dict:
+        """Times every launch shape that fits on n_trial sweeps and keeps the
+        fastest (spins saved and restored); returns the choice."""
+        wc, lut, cl, rate = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib().sqa_autotune(self._h, int(n_trial), _stream_ptr(stream), C.byref(wc), C.byref(lut),
+                                  C.byref(cl), C.byref(rate)), "sqa_autotune")
+        return {"words_per_unit": wc.value, "use_table": lut.value, "cluster": cl.value,
+                "trial_attempts_per_s": rate.value}
 
     def launch(self) -> dict:
         wc, lut, smem, cl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
@@ -345,6 +361,38 @@ def batch_run(handles, stream=None):
     """One persistent launch over every unit of several handles."""
     arr = (C.c_void_p * len(handles))(*[h.handle for h in handles])
     _check(lib().sqa_batch_run(arr, len(handles), _stream_ptr(stream)), "sqa_batch_run")
+
+
+class Batch:
+    """Several handles planned once for one persistent launch, replayed from
+    a CUDA graph.  The handles must stay open (and untuned) while it lives."""
+
+    def __init__(self, handles):
+        self._hs = list(handles)
+        arr = (C.c_void_p * len(self._hs))(*[h.handle for h in self._hs])
+        b = C.c_void_p()
+        _check(lib().sqa_batch_create(arr, len(self._hs), C.byref(b)), "sqa_batch_create")
+        self._b = b
+
+    def launch(self, stream=None):
+        _check(lib().sqa_batch_launch(self._b, _stream_ptr(stream)), "sqa_batch_launch")
+
+    def autotune(self, n_trial: int = 20, stream=None) -> dict:
+        wc, rate = C.c_int32(), C.c_double()
+        _check(lib().sqa_batch_autotune(self._b, int(n_trial), _stream_ptr(stream), C.byref(wc), C.byref(rate)),
+               "sqa_batch_autotune")
+        return {"words_per_unit": wc.value, "trial_attempts_per_s": rate.value}
+
+    def close(self):
+        if self._b:
+            lib().sqa_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ground_energy(N: int, J) -> np.ndarray:

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsqa_gb300.so")
-SOURCES = ("kernels.cu", "capi.cu", "host_plan.cpp", "intpeak.cu", "noalloc.cu", "server.cu")
+SOURCES = ("kernels.cu", "capi.cu", "host_plan.cpp", "intpeak.cu", "noalloc.cu", "server.cu", "batch.cu")
 HEADERS = ("philox.cuh", "sqa_internal.h", "layout.cuh", "handle.h")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

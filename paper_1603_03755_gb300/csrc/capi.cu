@@ -45,8 +45,6 @@ sqa_status cuda_fail(cudaError_t e, const char *where)
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
-constexpr int kThreads = 256;
-
 static int g_num_sms = 0;
 static int g_smem_limit = 0;  // dynamic shared memory one sweep block may use
 
@@ -423,7 +421,6 @@ int grid_for(const void *kernel, int smem_bytes, int n_units)
     return std::max(1, std::min(n_units, per_sm * g_num_sms));
 }
 
-// One launch of the sweep kernel over units [u0, u0+nu) of one handle.
 int64_t estimate_device_bytes(const sqa_desc *d)
 {
     if (validate(d) != SQA_OK) return 0;
@@ -455,6 +452,21 @@ int64_t estimate_device_bytes(const sqa_desc *d)
     b += d->embedding == SQA_EMB_ME_CHIMERA ? al((int64_t)pl.chain.size() * 4) : al((int64_t)pl.pair.size() * 4);
     b += al((int64_t)sizeof(JobDev)) + al((int64_t)I * W * (int64_t)sizeof(Unit)) + al(4);
     return b;
+}
+
+sqa_status plan_job(sqa_handle *h, int c_forced, int force_wc, JobDev &J, std::vector<Unit> &units)
+{
+    const int keep = h->force_wc;
+    h->force_wc = force_wc;
+    J = h->job;
+    const sqa_status st = plan_shape(h, c_forced, J, units);
+    h->force_wc = keep;
+    return st;
+}
+
+sqa_status run_sweeps(sqa_handle *h, int t0, int t1, cudaStream_t s)
+{
+    return launch_sweeps(h, t0, t1, 0, h->n_units, s);
 }
 
 cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s)

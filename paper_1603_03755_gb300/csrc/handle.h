@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <string>
 #include <vector>
 
 #include "sqa_internal.h"
@@ -45,7 +46,10 @@ struct sqa_handle {
 
 namespace sqa {
 
+constexpr int kThreads = 256;  // threads per block of every kernel here
+
 sqa_status device_ready();
+void set_error(const std::string &msg);
 sqa_status cuda_fail(cudaError_t e, const char *where);
 // Draws fresh initial spins for every instance of h on stream s.
 sqa_status launch_init(sqa_handle *h, cudaStream_t s);
@@ -60,5 +64,10 @@ int64_t estimate_device_bytes(const sqa_desc *d);
 void destroy_on_stream(sqa_handle *h, cudaStream_t s);
 // One launch of a job's own sweep kernel over all its units.
 cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s);
+// Plans h's launch (J, units) with c_forced blocks per cluster (0: any) and
+// force_wc words per unit (0: the planner's choice), without changing h.
+sqa_status plan_job(sqa_handle *h, int c_forced, int force_wc, JobDev &J, std::vector<Unit> &units);
+// Sweeps [t0, t1) of every unit of h with its current launch shape, on s.
+sqa_status run_sweeps(sqa_handle *h, int t0, int t1, cudaStream_t s);
 
 }  // namespace sqa

@@ -30,10 +30,6 @@
 
 #include "handle.h"
 
-namespace sqa {
-void set_error(const std::string &msg);
-}
-
 using namespace sqa;
 
 namespace {
