@@ -94,6 +94,24 @@ def test_vote_over_trees_majority():
         assert np.array_equal(O.lhz_vote_decode(N, trees, q), want)
 
 
+def test_two_tree_vote_is_the_first_tree():
+    """With an even number of trees a vertex can tie; a tie takes the first
+    tree's value (reading of Eq. 5).  So a two-tree vote is the first tree's
+    decode, on any state, with or without leakage."""
+    N = 7
+    pb = O.Problem("lhz", N, W.random_couplings(N, 5), 2)
+    rng = np.random.default_rng(8)
+    trees = np.stack([O.prufer_tree(N, 3, 0, t) for t in range(2)])
+    ties = 0
+    for _ in range(100):
+        q = _random_phys(pb, rng)
+        a, b = (O.lhz_tree_decode(N, p, q) for p in trees)
+        ties += int((a != b).sum())
+        assert np.array_equal(O.lhz_vote_decode(N, trees, q), a)
+        assert np.array_equal(O.lhz_vote_decode(N, trees[::-1].copy(), q), b)
+    assert ties > 0                                   # the states did exercise ties
+
+
 @pytest.mark.parametrize("N", [4, 8, 12, 16])
 def test_me_majority_vote(N):
     pb = O.Problem("me", N, W.random_couplings(N, 4), 2)
