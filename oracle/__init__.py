@@ -79,6 +79,11 @@ def _declare(L):
         "orc_tree_draw": (u32, [u64, i32, i32, i32, i32]),
         "orc_init_spins": (None, [P(_Problem), i32, i32, u64, i32, _i8p]),
         "orc_sqa_run": (i32, [P(_Problem), P(_SqaParams), _i8p, i32, i32, i32, i32, i32]),
+        "orc_sqa_wolff_run": (i32, [P(_Problem), P(_SqaParams), _i8p, i32, i32, i32, i32, i32]),
+        "orc_bond_threshold": (u32, [dbl, dbl, i32]),
+        "orc_wolff_start": (u32, [u64, u32, u32, u32, u32, i32]),
+        "orc_wolff_bond_uniform": (u32, [u64, u32, u32, i32, i32, u32, u32]),
+        "orc_wolff_accept_uniform": (u32, [u64, u32, u32, u32, u32]),
         "orc_pt_run": (i32, [P(_Problem), P(_PtParams), _i8p, _i64p, i32, i32, i32, i32, i32]),
         "orc_me_decode": (None, [i32, _i32p, _i32p, _i8p, _i8p]),
         "orc_prufer_tree": (None, [i32, u64, i32, i32, _i32p]),
@@ -239,6 +244,22 @@ def sweep_uniform(seed, t, slot, rho, inst) -> int:
     return int(lib().orc_sweep_uniform(seed, t, slot, rho, inst))
 
 
+def bond_threshold(beta: float, A: float, L: int) -> int:
+    return int(lib().orc_bond_threshold(float(beta), float(A), L))
+
+
+def wolff_start(seed, t, site, rho, inst, L) -> int:
+    return int(lib().orc_wolff_start(seed, t, site, rho, inst, L))
+
+
+def wolff_bond_uniform(seed, t, site, L, tau, rho, inst) -> int:
+    return int(lib().orc_wolff_bond_uniform(seed, t, site, L, tau, rho, inst))
+
+
+def wolff_accept_uniform(seed, t, site, rho, inst) -> int:
+    return int(lib().orc_wolff_accept_uniform(seed, t, site, rho, inst))
+
+
 def swap_uniform(seed, event, pair, rho, inst) -> int:
     return int(lib().orc_swap_uniform(seed, event, pair, rho, inst))
 
@@ -250,9 +271,15 @@ def init_spins(pb: Problem, Z: int, R: int, seed: int, inst: int) -> np.ndarray:
 
 
 class SQA:
-    """Path-integral SQA of one instance; state [L][n][R] int8."""
+    """Path-integral SQA of one instance; state [L][n][R] int8.  move is
+    "metropolis" (single-spin sweep) or "wolff" (one time-like cluster move
+    per site and replica per sweep)."""
 
-    def __init__(self, pb: Problem, L: int, R: int, beta: float, A, B, seed: int, inst: int = 0):
+    def __init__(self, pb: Problem, L: int, R: int, beta: float, A, B, seed: int, inst: int = 0,
+                 move: str = "metropolis"):
+        if move not in ("metropolis", "wolff"):
+            raise ValueError("move is 'metropolis' or 'wolff'")
+        self.move = move
         self.pb, self.L, self.R, self.beta, self.seed, self.inst = pb, L, R, beta, seed, inst
         self.A = np.ascontiguousarray(A, np.float64)
         self.B = np.ascontiguousarray(B, np.float64)
@@ -262,7 +289,8 @@ class SQA:
 
     def run(self, t0: int, t1: int, rho0: int = 0, rho1: int | None = None):
         rho1 = self.R if rho1 is None else rho1
-        rc = lib().orc_sqa_run(self.pb.c, C.byref(self._prm), self.s, self.inst, t0, t1, rho0, rho1)
+        run = lib().orc_sqa_wolff_run if self.move == "wolff" else lib().orc_sqa_run
+        rc = run(self.pb.c, C.byref(self._prm), self.s, self.inst, t0, t1, rho0, rho1)
         if rc != 0:
             raise ValueError("orc_sqa_run rejected its arguments")
         return self.s

@@ -118,6 +118,71 @@ int32_t orc_sqa_run(const orc_problem *pb, const orc_sqa_params *prm, int8_t *s,
     return 0;
 }
 
+uint32_t orc_bond_threshold(double beta, double A, int32_t L)
+{
+    double a = beta * A / (double)L;
+    if (a <= 0.0) return 0xFFFFFFFFu;
+    double v = floor(ldexp(1.0 - tanh(a), 32));
+    if (v >= 4294967294.0) return 0xFFFFFFFEu;
+    return (uint32_t)v;
+}
+
+/* Time-like cluster move (Sec. III, App. B: one cluster update along
+ * imaginary time per spatial site and sweep).  For replica rho of a site:
+ * a start slice tau0 is drawn; the cluster grows forward from tau0 through
+ * each bond (tau, tau+1) whose two slices carry equal spins and whose bond
+ * uniform is below the bond threshold (probability 1 - e^(-2 Jperp)), and
+ * stops at the first bond that does not join; it then grows backward from
+ * tau0 the same way, never past the forward end (at most L slices).  The
+ * temporal part of the action is accounted for by this construction, so the
+ * cluster is flipped with the Metropolis test on the problem part alone:
+ * accept iff x <= 0 or u < T(x), x = alpha * D, D the sum of the flip
+ * energies of the site over the cluster's slices (all taken before the flip;
+ * the site's terms lie within one slice).  Sites of one colour do not share a
+ * term, so a colour class moves in any order. */
+int32_t orc_sqa_wolff_run(const orc_problem *pb, const orc_sqa_params *prm, int8_t *s, int32_t inst,
+                          int32_t t0, int32_t t1, int32_t rho0, int32_t rho1)
+{
+    int32_t L = prm->L, R = prm->R, n = pb->n;
+    if (L < 2 || (L & 1) || t0 < 0 || t1 > prm->S || rho0 < 0 || rho1 > R) return -1;
+    for (int32_t t = t0; t < t1; t++) {
+        double alpha = prm->beta * prm->B[t] / (double)L;
+        uint32_t Tb = orc_bond_threshold(prm->beta, prm->A[t], L);
+        for (int32_t chi = 0; chi < pb->n_colours; chi++)
+            for (int32_t site = 0; site < n; site++) {
+                if (!pb->used[site] || pb->colour[site] != chi) continue;
+                for (int32_t rho = rho0; rho < rho1; rho++) {
+                    int32_t tau0 = (int32_t)orc_wolff_start(prm->seed, (uint32_t)t, (uint32_t)site, (uint32_t)rho,
+                                                            (uint32_t)inst, L);
+                    /* bond (tau, tau+1 mod L) joins */
+#define ORC_JOINS(tau)                                                                                 \
+    (*at(s, n, R, (tau), site, rho) == *at(s, n, R, ((tau) + 1) % L, site, rho) &&                      \
+     (Tb == 0xFFFFFFFFu ||                                                                             \
+      orc_wolff_bond_uniform(prm->seed, (uint32_t)t, (uint32_t)site, L, (tau), (uint32_t)rho, (uint32_t)inst) < Tb))
+                    int32_t fwd = 0;
+                    while (fwd < L - 1 && ORC_JOINS((tau0 + fwd) % L)) fwd++;
+                    int32_t back = 0;
+                    while (back < L - 1 - fwd && ORC_JOINS((tau0 - 1 - back + 2 * L) % L)) back++;
+#undef ORC_JOINS
+                    int64_t D = 0;
+                    for (int32_t q = -back; q <= fwd; q++) {
+                        int32_t tau = (tau0 + q + L) % L;
+                        D += orc_flip_delta(pb, s + (int64_t)tau * n * R, R, rho, site);
+                    }
+                    double x = alpha * (double)D;
+                    uint32_t u = orc_wolff_accept_uniform(prm->seed, (uint32_t)t, (uint32_t)site, (uint32_t)rho,
+                                                          (uint32_t)inst);
+                    if (x <= 0.0 || u < orc_threshold(x))
+                        for (int32_t q = -back; q <= fwd; q++) {
+                            int8_t *v = at(s, n, R, (tau0 + q + L) % L, site, rho);
+                            *v = (int8_t)-*v;
+                        }
+                }
+            }
+    }
+    return 0;
+}
+
 static void pt_energies(const orc_problem *pb, const int8_t *s, int32_t P, int32_t R,
                         int32_t rho0, int32_t rho1, int64_t *E)
 {

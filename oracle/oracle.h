@@ -36,6 +36,9 @@ extern "C" {
 #define ORC_DOM_SWEEP_LO 0x3C6EF372u
 #define ORC_DOM_SWAP 0xA54FF53Au
 #define ORC_DOM_TREE 0x510E527Fu
+#define ORC_DOM_WSTART 0x9B05688Cu
+#define ORC_DOM_WBOND 0x1F83D9ABu
+#define ORC_DOM_WACC 0x5BE0CD19u
 
 /* ---- Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11) ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -98,6 +101,17 @@ uint32_t orc_sweep_uniform(uint64_t seed, uint32_t t, uint32_t slot, uint32_t rh
 uint32_t orc_swap_uniform(uint64_t seed, uint32_t event, uint32_t pair, uint32_t rho, uint32_t inst);
 uint32_t orc_tree_draw(uint64_t seed, int32_t inst, int32_t tree, int32_t pos, int32_t N);
 /* Initial spins of a state [Z][n][R]; unused sites are +1. */
+/* Time-like cluster move streams (see anneal.c).  Start slice of replica
+ * rho's cluster at site (canonical index), sweep t: floor(u L / 2^32) with u
+ * word rho%4 of WSTART at counter (t, site, rho/4, inst).  Bond uniform of the
+ * bond between slices tau and tau+1 (mod L): a 32-bit number whose bit 31-k
+ * is bit rho%32 of bit-plane k, plane k being word k%4 of WBOND at counter
+ * (t, site*L + tau, (rho/32)*8 + k/4, inst).  Acceptance uniform: word rho%4
+ * of WACC at counter (t, site, rho/4, inst). */
+uint32_t orc_wolff_start(uint64_t seed, uint32_t t, uint32_t site, uint32_t rho, uint32_t inst, int32_t L);
+uint32_t orc_wolff_bond_uniform(uint64_t seed, uint32_t t, uint32_t site, int32_t L, int32_t tau, uint32_t rho,
+                                uint32_t inst);
+uint32_t orc_wolff_accept_uniform(uint64_t seed, uint32_t t, uint32_t site, uint32_t rho, uint32_t inst);
 void orc_init_spins(const orc_problem *pb, int32_t Z, int32_t R, uint64_t seed, int32_t inst,
                     int8_t *s);
 
@@ -113,6 +127,14 @@ typedef struct {
 } orc_sqa_params;
 int32_t orc_sqa_run(const orc_problem *pb, const orc_sqa_params *prm, int8_t *s, int32_t inst,
                     int32_t t0, int32_t t1, int32_t rho0, int32_t rho1);
+/* Probability threshold of joining two equal neighbouring slices into one
+ * time-like cluster: p = 1 - e^(-2 Jperp) = 1 - tanh(beta A / L);
+ * 0xFFFFFFFF (always) when A <= 0, else min(floor(2^32 p), 2^32 - 2). */
+uint32_t orc_bond_threshold(double beta, double A, int32_t L);
+/* The same anneal with one time-like cluster move per (site, replica) per
+ * sweep instead of the single-spin sweep. */
+int32_t orc_sqa_wolff_run(const orc_problem *pb, const orc_sqa_params *prm, int8_t *s, int32_t inst,
+                          int32_t t0, int32_t t1, int32_t rho0, int32_t rho1);
 
 /* ---- PT: sweeps t0..t1-1 on state [P][n][R]; E [P][R] written at exit ---- */
 typedef struct {

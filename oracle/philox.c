@@ -73,6 +73,37 @@ uint32_t orc_swap_uniform(uint64_t seed, uint32_t event, uint32_t pair, uint32_t
     return out[rho & 3u];
 }
 
+uint32_t orc_wolff_start(uint64_t seed, uint32_t t, uint32_t site, uint32_t rho, uint32_t inst, int32_t L)
+{
+    uint32_t ctr[4] = {t, site, rho >> 2, inst};
+    uint32_t key[2], out[4];
+    stream_key(seed, ORC_DOM_WSTART, key);
+    orc_philox4x32_10(ctr, key, out);
+    return (uint32_t)(((uint64_t)out[rho & 3u] * (uint64_t)L) >> 32);
+}
+
+uint32_t orc_wolff_bond_uniform(uint64_t seed, uint32_t t, uint32_t site, int32_t L, int32_t tau, uint32_t rho,
+                                uint32_t inst)
+{
+    uint32_t key[2], out[4], u = 0;
+    stream_key(seed, ORC_DOM_WBOND, key);
+    for (uint32_t k = 0; k < 32; k++) {
+        uint32_t ctr[4] = {t, site * (uint32_t)L + (uint32_t)tau, (rho >> 5) * 8u + (k >> 2), inst};
+        orc_philox4x32_10(ctr, key, out);
+        u |= ((out[k & 3u] >> (rho & 31u)) & 1u) << (31u - k);
+    }
+    return u;
+}
+
+uint32_t orc_wolff_accept_uniform(uint64_t seed, uint32_t t, uint32_t site, uint32_t rho, uint32_t inst)
+{
+    uint32_t ctr[4] = {t, site, rho >> 2, inst};
+    uint32_t key[2], out[4];
+    stream_key(seed, ORC_DOM_WACC, key);
+    orc_philox4x32_10(ctr, key, out);
+    return out[rho & 3u];
+}
+
 /* Initial spin of (site, z, replica rho): bit (rho % 32) of output word
  * (rho/32) % 4 of the INIT stream at counter (site, z, rho/128, inst). */
 void orc_init_spins(const orc_problem *pb, int32_t Z, int32_t R, uint64_t seed, int32_t inst,

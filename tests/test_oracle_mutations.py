@@ -17,7 +17,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ["test_oracle_rng.py", "test_oracle_embedding.py", "test_oracle_tables.py",
-             "test_oracle_decode.py", "test_oracle_statistics.py"]
+             "test_oracle_decode.py", "test_oracle_statistics.py", "test_oracle_wolff.py"]
 
 # (name, file, original text, planted mistake)
 MUTANTS = [
@@ -41,7 +41,11 @@ MUTANTS = [
     ("flip energy sign", "embed.c", "return -2 * before;", "return 2 * before;"),
     ("Jperp sign", "anneal.c", "return -0.5 * log(tanh(a));", "return 0.5 * log(tanh(a));"),
     ("alpha without 1/L in the sweep", "anneal.c",
-     "double alpha = prm->beta * prm->B[t] / (double)L;", "double alpha = prm->beta * prm->B[t];"),
+     "double alpha = prm->beta * prm->B[t] / (double)L;\n        double jp",
+     "double alpha = prm->beta * prm->B[t];\n        double jp"),
+    ("alpha without 1/L in the cluster move", "anneal.c",
+     "double alpha = prm->beta * prm->B[t] / (double)L;\n        uint32_t Tb",
+     "double alpha = prm->beta * prm->B[t];\n        uint32_t Tb"),
     ("temporal term without its factor 2", "anneal.c",
      "xt = 2.0 * jperp * (double)m;", "xt = jperp * (double)m;"),
     ("open instead of periodic imaginary time", "anneal.c",
@@ -58,6 +62,16 @@ MUTANTS = [
     ("ME chain loses a vertical coupler", "embed.c",
      "for (int32_t r = 0; r < g; r++) {\n            int32_t mem[2]",
      "for (int32_t r = 0; r + 1 < g; r++) {\n            int32_t mem[2]"),
+    ("cluster bond probability e^(-2 Jperp)", "anneal.c",
+     "double v = floor(ldexp(1.0 - tanh(a), 32));", "double v = floor(ldexp(tanh(a), 32));"),
+    ("cluster grows forward only", "anneal.c",
+     "while (back < L - 1 - fwd && ORC_JOINS(", "while (0 && ORC_JOINS("),
+    ("cluster bonds ignore spin equality", "anneal.c",
+     "(*at(s, n, R, (tau), site, rho) == *at(s, n, R, ((tau) + 1) % L, site, rho) &&",
+     "(1 &&"),
+    ("cluster energy taken from its start slice only", "anneal.c",
+     "D += orc_flip_delta(pb, s + (int64_t)tau * n * R, R, rho, site);",
+     "D += orc_flip_delta(pb, s + (int64_t)tau0 * n * R, R, rho, site);"),
     ("ME majority-vote tie rule", "decode.c", "logical[i] = phys[hub[i]];", "logical[i] = 1;"),
     ("LHZ tree vote tie rule", "decode.c", "(sum < 0 ? -1 : tmp[i])", "(sum < 0 ? -1 : 1)"),
     ("ground-state enumeration half short", "decode.c",
