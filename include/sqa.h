@@ -56,6 +56,12 @@ typedef enum {
 
 typedef enum { SQA_EMB_ME_CHIMERA = 0, SQA_EMB_LHZ = 1 } sqa_embedding;
 typedef enum { SQA_KIND_SQA = 0, SQA_KIND_PT = 1 } sqa_kind;
+/* SQA update move.  METROPOLIS: single-spin Metropolis sweeps over every
+ * (site, slice).  WOLFF: one time-like cluster move per (site, replica) per
+ * sweep (Sec. III, App. B): bonds between equal neighbouring slices join with
+ * probability 1 - e^(-2 Jperp), the cluster grown from a random slice is
+ * flipped with the Metropolis test on its problem-energy change. */
+typedef enum { SQA_MOVE_METROPOLIS = 0, SQA_MOVE_WOLFF = 1 } sqa_move;
 typedef enum {
     SQA_DECODE_ME_MV = 0,     /* ME majority vote per chain (Eq. 4); ties -> hub spin */
     SQA_DECODE_LHZ_TREES = 1, /* LHZ majority vote over n_trees random trees (Eq. 5) */
@@ -85,6 +91,8 @@ typedef struct {
     int32_t n_temps;       /* P >= 1 */
     const double *betas;   /* [P] strictly decreasing (coldest first), > 0 */
     int32_t swap_every;    /* >= 1 sweeps between swap events */
+    /* SQA move (sqa_move; 0 = METROPOLIS).  WOLFF needs L <= 128. */
+    int32_t move;
 } sqa_desc;
 
 typedef struct sqa_handle sqa_handle;
@@ -284,6 +292,14 @@ int64_t sqa_plan_device_bytes(const sqa_desc *desc);
  * by (delta - dmin)/2, nd = (dmax - dmin)/2 + 1.  cap is the length of T. */
 sqa_status sqa_plan_tables(const sqa_desc *desc, uint32_t *T, int64_t cap, int32_t *dmin,
                            int32_t *dmax);
+
+/* The cluster-move tables sqa_create would upload for an SQA desc with
+ * move = SQA_MOVE_WOLFF: Tb [S] bond thresholds; acc_off, acc_len [S] and
+ * Tacc (cap entries) the acceptance thresholds T(alpha_t D) of sweep t for
+ * D = 2, 4, ..., 2 acc_len[t] at Tacc[acc_off[t] + D/2 - 1]; *n_acc gets the
+ * total.  Any output may be NULL to query sizes. */
+sqa_status sqa_plan_wolff_tables(const sqa_desc *desc, uint32_t *Tb, int32_t *acc_off, int32_t *acc_len,
+                                 uint32_t *Tacc, int64_t cap, int64_t *n_acc);
 
 /* PT swap thresholds of slots (pair, pair+1) (Eq. 9): out[dE-1] for
  * dE = 1..*len, zero beyond. */

@@ -20,6 +20,7 @@ SQA_OK, SQA_ERR_INVALID, SQA_ERR_UNSUPPORTED, SQA_ERR_NOMEM = 0, -1, -2, -3
 SQA_ERR_CUDA, SQA_ERR_TIMEOUT, SQA_ERR_NO_DEVICE, SQA_ERR_BUSY = -4, -5, -6, -7
 EMB = {"me": 0, "lhz": 1}
 KIND = {"sqa": 0, "pt": 1}
+MOVE = {"metropolis": 0, "wolff": 1}
 DECODE = {"me_mv": 0, "lhz_trees": 1, "lhz_star": 2, "lhz_chain": 3}
 
 LIB_PATH = _build.LIB
@@ -37,7 +38,7 @@ class _Desc(C.Structure):
                 ("penalty", C.c_int32), ("n_sweeps", C.c_int32), ("n_replicas", C.c_int32),
                 ("seed", C.c_uint64), ("n_slices", C.c_int32), ("beta", C.c_double),
                 ("A", C.c_void_p), ("B", C.c_void_p), ("n_temps", C.c_int32),
-                ("betas", C.c_void_p), ("swap_every", C.c_int32)]
+                ("betas", C.c_void_p), ("swap_every", C.c_int32), ("move", C.c_int32)]
 
 
 class _Info(C.Structure):
@@ -79,6 +80,8 @@ _SIGS = {
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sqa_plan_tables": (C.c_int, [C.POINTER(_Desc), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "sqa_plan_swap_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_plan_wolff_tables": (C.c_int, [C.POINTER(_Desc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_int64, C.POINTER(C.c_int64)]),
     "sqa_plan_tree": (C.c_int, [C.c_int32, C.c_uint64, C.c_int32, C.c_int32, C.c_void_p]),
     "sqa_int_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
     "sqa_server_create": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_void_p)]),
@@ -138,7 +141,7 @@ def _ptr(x):
 
 def _make_desc(*, embedding: str, N: int, J, penalty: int, sweeps: int, R: int, seed: int = 0,
                kind: str = "sqa", L: int = 32, beta: float = 1.0, A=None, B=None, betas=None,
-               swap_every: int = 1):
+               swap_every: int = 1, move: str = "metropolis"):
     """An sqa_desc and the arrays it points into (keep them alive)."""
     J = np.ascontiguousarray(np.atleast_2d(np.asarray(J, np.int32)))
     keep = [J]
@@ -158,6 +161,7 @@ def _make_desc(*, embedding: str, N: int, J, penalty: int, sweeps: int, R: int, 
         keep.append(betas)
         d.betas, d.n_temps = betas.ctypes.data, len(betas)
     d.swap_every = int(swap_every)
+    d.move = MOVE[move]
     meta = {"N": N, "I": J.shape[0], "R": int(R), "kind": kind, "embedding": embedding,
             "Z": int(L) if kind == "sqa" else (len(betas) if betas is not None else 0)}
     return d, keep, meta

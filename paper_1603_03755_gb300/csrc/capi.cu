@@ -62,8 +62,8 @@ sqa_status device_ready()
         SQA_CUDA(cudaGetDeviceProperties(&prop, dev));
         cudaFuncAttributes fa;
         SQA_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel));
-        const void *ks[4] = {(const void *)sweep_kernel, sweep_one_entry_mode(0), sweep_one_entry_mode(1),
-                             sweep_one_entry_mode(2)};
+        const void *ks[6] = {(const void *)sweep_kernel,   sweep_one_entry_mode(0), sweep_one_entry_mode(1),
+                             sweep_one_entry_mode(2), sweep_one_entry_mode(3), sweep_one_entry_mode(4)};
         int limit = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
         for (const void *k : ks) {
             cudaFuncAttributes fk;
@@ -169,11 +169,13 @@ sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> 
         int C = 0, wc = 0, lut = 0;
     } best;
     const int cmax = c_forced > 0 ? c_forced : 8;
+    const bool wolff = J.kind == SQA_KIND_SQA && J.move == SQA_MOVE_WOLFF;
     for (int C = c_forced > 0 ? c_forced : 1; C <= cmax; C *= 2) {
         if (J.kind == SQA_KIND_SQA ? (J.Z % (2 * C)) : (J.Z % C)) continue;
+        if (wolff && C > 1) continue;  // a cluster move needs the whole ring in one block
         J.csize = C;
         J.zr = J.Z / C;
-        const int modes = J.kind == SQA_KIND_SQA ? 2 : 1;
+        const int modes = J.kind == SQA_KIND_SQA && !wolff ? 2 : 1;
         for (int m = modes - 1; m >= 0; m--) {
             J.use_lut = J.kind == SQA_KIND_SQA ? m : 0;
             if (!J.use_lut && h->window_limit_exceeded) continue;
@@ -235,6 +237,9 @@ sqa_status validate(const sqa_desc *d)
         for (int64_t i = 0; i < (int64_t)d->n_instances * d->n_logical; i++)
             if (d->h[i] != 0) return set_error("non-zero logical fields need an ancilla"), SQA_ERR_UNSUPPORTED;
     }
+    if (d->move != SQA_MOVE_METROPOLIS && d->move != SQA_MOVE_WOLFF) return set_error("move"), SQA_ERR_INVALID;
+    if (d->kind == SQA_KIND_SQA && d->move == SQA_MOVE_WOLFF && d->n_slices > 128)
+        return set_error("cluster moves need n_slices <= 128"), SQA_ERR_UNSUPPORTED;
     if (d->kind == SQA_KIND_SQA) {
         if (d->n_slices < 2 || (d->n_slices & 1) || d->n_slices > 1024)
             return set_error("n_slices must be even, 2..1024"), SQA_ERR_INVALID;
@@ -266,7 +271,8 @@ sqa_status setup_program(sqa_handle *h)
     const int K = h->kind == SQA_KIND_SQA ? 6 : 2;
     // byte-wise windows hold K*S_i (+2 for SQA) per site; the SQA table mode
     // has no such limit
-    h->window_limit_exceeded = K * h->smax + 2 > kMaxByteWindow;
+    const bool wolff = h->kind == SQA_KIND_SQA && h->move == SQA_MOVE_WOLFF;
+    h->window_limit_exceeded = !wolff && K * h->smax + 2 > kMaxByteWindow;
     if (h->window_limit_exceeded && h->kind == SQA_KIND_PT) {
         set_error("penalty/couplings too large for the byte-wise threshold window");
         return SQA_ERR_UNSUPPORTED;
@@ -301,6 +307,10 @@ sqa_status setup_program(sqa_handle *h)
     J.key_hi = shi ^ kDomSweepHi;
     J.key_lo = shi ^ kDomSweepLo;
     J.key_swap = shi ^ kDomSwap;
+    J.move = wolff ? SQA_MOVE_WOLFF : SQA_MOVE_METROPOLIS;
+    J.key_wstart = shi ^ kDomWStart;
+    J.key_wbond = shi ^ kDomWBond;
+    J.key_wacc = shi ^ kDomWAcc;
 
     std::vector<SiteRec> sites, all_sites;
     std::vector<ETerm> et, all_et;
@@ -319,9 +329,13 @@ sqa_status setup_program(sqa_handle *h)
         all_et.insert(all_et.end(), et.begin(), et.end());
         all_ec.insert(all_ec.end(), ec.begin(), ec.end());
     }
-    std::vector<uint32_t> T, Tsw;
-    std::vector<int> swoff, swlen;
-    if (h->kind == SQA_KIND_SQA) {
+    h->d_T = h->d_Tsw = h->d_Tb = h->d_Tacc = nullptr;
+    h->d_swoff = h->d_swlen = h->d_accoff = h->d_acclen = nullptr;
+    std::vector<uint32_t> T, Tsw, Tb, Tacc;
+    std::vector<int> swoff, swlen, accoff, acclen;
+    if (wolff) {
+        wolff_tables(h->A.data(), h->B.data(), h->beta, h->L, h->S, h->dmax, Tb, Tacc, accoff, acclen);
+    } else if (h->kind == SQA_KIND_SQA) {
         sqa_tables(h->A.data(), h->B.data(), h->beta, h->L, h->S, h->dmin, h->dmax, T);
     } else {
         pt_tables(h->betas.data(), h->P, h->dmin, h->dmax, T);
@@ -333,7 +347,14 @@ sqa_status setup_program(sqa_handle *h)
     if ((st = upload(h, &h->d_eterms, all_et)) != SQA_OK) return st;
     if ((st = upload(h, &h->d_ecls, all_ec)) != SQA_OK) return st;
     J.n_ecls = ecls_ok ? n_ecls : 0;
-    if ((st = upload(h, &h->d_T, T)) != SQA_OK) return st;
+    if (wolff) {
+        if ((st = upload(h, &h->d_Tb, Tb)) != SQA_OK) return st;
+        if ((st = upload(h, &h->d_Tacc, Tacc)) != SQA_OK) return st;
+        if ((st = upload(h, &h->d_accoff, accoff)) != SQA_OK) return st;
+        if ((st = upload(h, &h->d_acclen, acclen)) != SQA_OK) return st;
+    } else if ((st = upload(h, &h->d_T, T)) != SQA_OK) {
+        return st;
+    }
     if (h->kind == SQA_KIND_PT) {
         if ((st = upload(h, &h->d_Tsw, Tsw)) != SQA_OK) return st;
         if ((st = upload(h, &h->d_swoff, swoff)) != SQA_OK) return st;
@@ -356,6 +377,10 @@ sqa_status setup_program(sqa_handle *h)
     J.Tsw = h->d_Tsw;
     J.sw_off = h->d_swoff;
     J.sw_len = h->d_swlen;
+    J.Tb = h->d_Tb;
+    J.Tacc = h->d_Tacc;
+    J.acc_off = h->d_accoff;
+    J.acc_len = h->d_acclen;
     if ((st = plan_units(h)) != SQA_OK) return st;
     if ((st = dalloc(h, &h->d_job, 1)) != SQA_OK) return st;
     if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) return st;
@@ -439,7 +464,18 @@ int64_t estimate_device_bytes(const sqa_desc *d)
     b += al((int64_t)I * pl.n * (int64_t)sizeof(SiteRec));           // site records
     b += al((int64_t)I * (int64_t)pl.terms.size() * (int64_t)sizeof(ETerm));
     b += al((int64_t)I * kMaxEClasses * (int64_t)sizeof(EClass));
-    if (d->kind == SQA_KIND_SQA) {
+    if (d->kind == SQA_KIND_SQA && d->move == SQA_MOVE_WOLFF) {
+        std::vector<double> A(d->n_sweeps), B(d->n_sweeps);
+        for (int t = 0; t < d->n_sweeps; t++) {
+            const double s = ((double)t + 0.5) / (double)d->n_sweeps;
+            A[t] = d->A ? d->A[t] : 1.0 - s;
+            B[t] = d->B ? d->B[t] : s;
+        }
+        std::vector<uint32_t> Tb, Tacc;
+        std::vector<int> off, len;
+        wolff_tables(A.data(), B.data(), d->beta, d->n_slices, d->n_sweeps, 2 * smax, Tb, Tacc, off, len);
+        b += al((int64_t)Tb.size() * 4) + al((int64_t)Tacc.size() * 4) + 2 * al((int64_t)off.size() * 4);
+    } else if (d->kind == SQA_KIND_SQA) {
         b += al((int64_t)d->n_sweeps * 3 * nd * 4);                  // thresholds
     } else {
         b += al((int64_t)d->n_temps * nd * 4);
@@ -520,6 +556,7 @@ sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
     const int npair = h->N * (h->N - 1) / 2;
     h->J.assign(d->J, d->J + (size_t)h->I * npair);
     if (d->kind == SQA_KIND_SQA) {
+        h->move = d->move;
         h->L = d->n_slices;
         h->beta = d->beta;
         h->A.resize(h->S);
@@ -960,6 +997,41 @@ sqa_status sqa_plan_tables(const sqa_desc *d, uint32_t *T, int64_t cap, int32_t 
     if (!T) return SQA_OK;
     if ((int64_t)tab.size() > cap) return set_error("cap too small"), SQA_ERR_INVALID;
     memcpy(T, tab.data(), tab.size() * 4);
+    return SQA_OK;
+}
+
+sqa_status sqa_plan_wolff_tables(const sqa_desc *d, uint32_t *Tb, int32_t *acc_off, int32_t *acc_len,
+                                 uint32_t *Tacc, int64_t cap, int64_t *n_acc)
+{
+    sqa_status st = validate(d);
+    if (st != SQA_OK) return st;
+    if (d->kind != SQA_KIND_SQA) return set_error("cluster moves are SQA only"), SQA_ERR_INVALID;
+    Plan pl;
+    std::string err;
+    if (!build_plan(d->embedding, d->n_logical, pl, err)) return set_error(err), SQA_ERR_INVALID;
+    const int npair = d->n_logical * (d->n_logical - 1) / 2;
+    int smax = 0;
+    for (int i = 0; i < d->n_instances; i++)
+        smax = std::max(smax, site_weight_sum_max(pl, d->J + (size_t)i * npair, d->penalty));
+    std::vector<double> A(d->n_sweeps), B(d->n_sweeps);
+    for (int t = 0; t < d->n_sweeps; t++) {
+        const double s = ((double)t + 0.5) / (double)d->n_sweeps;
+        A[t] = d->A ? d->A[t] : 1.0 - s;
+        B[t] = d->B ? d->B[t] : s;
+    }
+    std::vector<uint32_t> tb, tacc;
+    std::vector<int> off, len;
+    wolff_tables(A.data(), B.data(), d->beta, d->n_slices, d->n_sweeps, 2 * smax, tb, tacc, off, len);
+    int64_t total = 0;
+    for (int x : len) total += x;
+    if (n_acc) *n_acc = total;
+    if (Tb) memcpy(Tb, tb.data(), tb.size() * 4);
+    if (acc_off) memcpy(acc_off, off.data(), off.size() * 4);
+    if (acc_len) memcpy(acc_len, len.data(), len.size() * 4);
+    if (Tacc) {
+        if (total > cap) return set_error("cap too small"), SQA_ERR_INVALID;
+        memcpy(Tacc, tacc.data(), (size_t)total * 4);
+    }
     return SQA_OK;
 }
 

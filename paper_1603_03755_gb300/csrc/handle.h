@@ -11,6 +11,7 @@
 struct sqa_handle {
     // copied description
     int kind = 0, emb = 0, N = 0, I = 0, penalty = 0, S = 0, R = 0, L = 0, P = 0, swap_every = 1;
+    int move = 0;  // SQA: sqa_move
     uint64_t seed = 0;
     double beta = 0;
     std::vector<int32_t> J;
@@ -27,6 +28,8 @@ struct sqa_handle {
     sqa::ETerm *d_eterms = nullptr;
     sqa::EClass *d_ecls = nullptr;
     uint32_t *d_Tsw = nullptr;
+    uint32_t *d_Tb = nullptr, *d_Tacc = nullptr;
+    int *d_accoff = nullptr, *d_acclen = nullptr;
     int *d_swoff = nullptr, *d_swlen = nullptr;
     int *d_canon = nullptr, *d_compact = nullptr;
     int32_t *d_J = nullptr;

@@ -312,6 +312,59 @@ void sqa_tables(const double *A, const double *B, double beta, int L, int S, int
     for (auto &th : pool) th.join();
 }
 
+uint32_t bond_threshold(double beta, double A, int L)
+{
+    const double a = beta * A / (double)L;
+    if (a <= 0.0) return 0xFFFFFFFFu;
+    const double v = floor(ldexp(1.0 - tanh(a), 32));
+    if (v >= 4294967294.0) return 0xFFFFFFFEu;
+    return (uint32_t)v;
+}
+
+void wolff_tables(const double *A, const double *B, double beta, int L, int S, int dmax, std::vector<uint32_t> &Tb,
+                  std::vector<uint32_t> &Tacc, std::vector<int> &off, std::vector<int> &len)
+{
+    Tb.assign(S, 0);
+    off.assign(S, 0);
+    len.assign(S, 0);
+    const int64_t half_max = (int64_t)L * std::max(dmax, 0) / 2;  // D/2 of the largest cluster change
+    // rows are independent: split the sweeps over host threads, then join
+    int nthr = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+    if ((int64_t)S * std::min<int64_t>(half_max, 64) < (1 << 16)) nthr = 1;
+    std::vector<std::vector<uint32_t>> part(nthr);
+    auto rows = [&](int k, int t0, int t1) {
+        for (int t = t0; t < t1; t++) {
+            Tb[t] = bond_threshold(beta, A[t], L);
+            const double alpha = beta * B[t] / (double)L;
+            int n = 0;
+            for (int64_t d = 1; d <= half_max; d++) {
+                const uint32_t T = threshold(alpha * (double)(2 * d));
+                if (T == 0) break;
+                part[k].push_back(T);
+                n++;
+            }
+            len[t] = n;
+        }
+    };
+    std::vector<std::thread> pool;
+    std::vector<int> t_lo(nthr + 1);
+    for (int k = 0; k <= nthr; k++) t_lo[k] = (int)((int64_t)S * k / nthr);
+    if (nthr == 1)
+        rows(0, 0, S);
+    else {
+        for (int k = 0; k < nthr; k++) pool.emplace_back(rows, k, t_lo[k], t_lo[k + 1]);
+        for (auto &th : pool) th.join();
+    }
+    Tacc.clear();
+    for (int k = 0; k < nthr; k++) Tacc.insert(Tacc.end(), part[k].begin(), part[k].end());
+    int o = 0;
+    for (int t = 0; t < S; t++) {
+        off[t] = o;
+        o += len[t];
+    }
+    if (Tacc.empty()) Tacc.push_back(0);  // keep one element so the upload is never empty
+}
+
 void pt_tables(const double *betas, int P, int dmin, int dmax, std::vector<uint32_t> &T)
 {
     const int nd = (dmax - dmin) / 2 + 1;

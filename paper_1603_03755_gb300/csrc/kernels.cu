@@ -533,6 +533,250 @@ __device__ void pt_swap(const JobDev &J, const Smem &sm, const Part &pt, int ins
     cluster_barrier(pt.C);  // swapped words are visible before the next sweep
 }
 
+// ---------------------------------------------------------------------------
+// Time-like cluster (Wolff) moves.  One warp moves one (site, word): lane l
+// holds slices l*SPL .. l*SPL+SPL-1 of the site's imaginary-time ring, and
+// after the energy transpose lane l also stands for replica l of the word.
+// ---------------------------------------------------------------------------
+
+// 32 x 32 bit transpose across the warp: afterwards bit j of lane i's word is
+// bit i of lane j's input word (five butterfly stages of block swaps).
+__device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const uint32_t m = d == 16 ? 0x0000FFFFu : d == 8 ? 0x00FF00FFu : d == 4 ? 0x0F0F0F0Fu : d == 2 ? 0x33333333u
+                                                                                                   : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, d);
+        x = (lane & d) ? ((x & ~m) | ((y >> d) & m)) : ((x & m) | ((y & m) << d));
+    }
+    return x;
+}
+
+// Replicas of und whose bond uniform is below T, compared bit-serially from
+// the most significant bit: bit 31-k of replica b's uniform is bit b of
+// plane k, plane k being word k%4 of the bond stream at counter
+// (t, slot, g8 + k/4, inst).  Planes are drawn only while some replica of
+// und is undecided.
+__device__ __forceinline__ uint32_t bond_below(uint32_t und, uint32_t T, uint32_t t, uint32_t slot, uint32_t g8,
+                                               uint32_t inst, uint32_t k0, uint32_t kb)
+{
+    uint32_t lt = 0u;
+    for (int q = 0; q < 8 && und; q++) {
+        const U4 P = philox(t, slot, g8 + (uint32_t)q, inst, k0, kb);
+#pragma unroll
+        for (int kk = 0; kk < 4; kk++) {
+            const uint32_t r = word_of(P, kk);
+            if ((T >> (31 - (4 * q + kk))) & 1u) {
+                lt |= und & ~r;
+                und &= r;
+            } else {
+                und &= ~r;
+            }
+        }
+    }
+    return lt;
+}
+
+// One cluster move for every replica of word w of site si (one warp).
+template <int SPL>
+__device__ __forceinline__ void wolff_item(const JobDev &J, const Smem &sm, uint32_t *start, int inst, int w0, int wc,
+                                           int t, int si, int w, uint32_t Tb, int aoff, int alen, int lane)
+{
+    const SiteRec &sr = sm.sites[si];
+    const int L = J.Z;
+    const int idx = si * wc + w;
+    const int gw = w0 + w;
+    const uint32_t canon = (uint32_t)sr.canon;
+    const uint32_t full = 0xFFFFFFFFu;
+    uint32_t s[SPL], A[SPL], St[SPL], C[SPL];
+    // spins and bonds of this lane's slices; bond j joins slice tau_j to tau_j + 1
+#pragma unroll
+    for (int j = 0; j < SPL; j++) {
+        const int tau = lane * SPL + j;
+        s[j] = 0u;
+        A[j] = 0u;
+        if (tau < L) {
+            s[j] = sm.S[(size_t)tau * J.zstride + idx];
+            const uint32_t nx = sm.S[(size_t)(tau + 1 == L ? 0 : tau + 1) * J.zstride + idx];
+            const uint32_t eq = ~(s[j] ^ nx);
+            A[j] = Tb == 0xFFFFFFFFu ? eq
+                                     : bond_below(eq, Tb, (uint32_t)t, canon * (uint32_t)L + (uint32_t)tau,
+                                                  (uint32_t)gw * 8u, (uint32_t)inst, J.seed_lo, J.key_wbond);
+        }
+    }
+    // start slice of replica `lane`, gathered into per-slice start masks
+    {
+        const uint32_t rho = (uint32_t)gw * 32u + (uint32_t)lane;
+        const U4 P = philox((uint32_t)t, canon, rho >> 2, (uint32_t)inst, J.seed_lo, J.key_wstart);
+        const int tau0 = (int)__umulhi(word_of(P, (int)(rho & 3u)), (uint32_t)L);
+#pragma unroll
+        for (int j = 0; j < SPL; j++) start[lane * SPL + j] = 0u;
+        __syncwarp();
+        const uint32_t same = __match_any_sync(full, tau0);
+        if (lane == __ffs(same) - 1) start[tau0] = same;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < SPL; j++) St[j] = lane * SPL + j < L ? start[lane * SPL + j] : 0u;
+    }
+    // growth along the ring as two scans of x -> G | (x & P) maps
+    const int last_lane = (L - 1) / SPL, last_slot = (L - 1) % SPL;
+    uint32_t Awrap = 0u;  // bond (L-1 -> 0), held by the owner of slice L-1
+#pragma unroll
+    for (int j = 0; j < SPL; j++)
+        if (j == last_slot) Awrap = A[j];
+    Awrap = __shfl_sync(full, Awrap, last_lane);
+    uint32_t Ain0 = __shfl_up_sync(full, A[SPL - 1], 1);  // bond into this lane's first slice
+    if (lane == 0) Ain0 = Awrap;
+    uint32_t F[SPL];
+    {
+        // forward: x_tau = St_tau | (x_{tau-1} & A_{tau-1})
+        uint32_t P = full, G = 0u;
+#pragma unroll
+        for (int j = 0; j < SPL; j++)
+            if (lane * SPL + j < L) {
+                const uint32_t a = j == 0 ? Ain0 : A[j - 1];
+                G = St[j] | (G & a);
+                P &= a;
+            }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t Pu = __shfl_up_sync(full, P, d), Gu = __shfl_up_sync(full, G, d);
+            if (lane >= d) {
+                G |= Gu & P;
+                P &= Pu;
+            }
+        }
+        const uint32_t wrap = __shfl_sync(full, G, 31);  // slice L-1 after one pass from zero
+        uint32_t Pex = __shfl_up_sync(full, P, 1), Gex = __shfl_up_sync(full, G, 1);
+        if (lane == 0) {
+            Pex = full;
+            Gex = 0u;
+        }
+        uint32_t x = Gex | (wrap & Pex);
+#pragma unroll
+        for (int j = 0; j < SPL; j++) {
+            F[j] = 0u;
+            if (lane * SPL + j < L) {
+                x = St[j] | (x & (j == 0 ? Ain0 : A[j - 1]));
+                F[j] = x;
+            }
+        }
+    }
+    {
+        // backward: x_tau = St_tau | (x_{tau+1} & A_tau)
+        uint32_t P = full, G = 0u;
+#pragma unroll
+        for (int j = SPL - 1; j >= 0; j--)
+            if (lane * SPL + j < L) {
+                G = St[j] | (G & A[j]);
+                P &= A[j];
+            }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t Pd = __shfl_down_sync(full, P, d), Gd = __shfl_down_sync(full, G, d);
+            if (lane + d < 32) {
+                G |= Gd & P;
+                P &= Pd;
+            }
+        }
+        const uint32_t wrap = __shfl_sync(full, G, 0);  // slice 0 after one pass from zero
+        uint32_t Pex = __shfl_down_sync(full, P, 1), Gex = __shfl_down_sync(full, G, 1);
+        if (lane == 31) {
+            Pex = full;
+            Gex = 0u;
+        }
+        uint32_t x = Gex | (wrap & Pex);
+#pragma unroll
+        for (int j = SPL - 1; j >= 0; j--) {
+            C[j] = F[j];
+            if (lane * SPL + j < L) {
+                x = St[j] | (x & A[j]);
+                C[j] |= x;
+            }
+        }
+    }
+    // problem-energy change of each replica's cluster: lane b counts, over the
+    // cluster's slices, the negative terms (per term) and the slices
+    int cnt_c = 0, D6 = 0;
+    {
+#pragma unroll
+        for (int j = 0; j < SPL; j++) cnt_c += __popc(warp_transpose(C[j], lane));
+        for (int k = 0; k < sr.nterm; k++) {
+            const TermRec tr = sr.t[k];
+            int cnt = 0;
+#pragma unroll
+            for (int j = 0; j < SPL; j++) {
+                const int tau = lane * SPL + j;
+                uint32_t v = 0u;
+                if (tau < L) {
+                    const uint32_t *row = sm.S + (size_t)tau * J.zstride;
+                    v = s[j];
+                    if (tr.p[0] >= 0) v ^= row[tr.p[0] * wc + w];
+                    if (tr.p[1] >= 0) v ^= row[tr.p[1] * wc + w];
+                    if (tr.p[2] >= 0) v ^= row[tr.p[2] * wc + w];
+                    v = (v ^ (uint32_t)((int)tr.w >> 31)) & C[j];  // term negative, slice in the cluster
+                }
+                cnt += __popc(warp_transpose(v, lane));
+            }
+            const int aw = tr.w < 0 ? -tr.w : tr.w;  // 6 |w|
+            D6 += aw * (4 * cnt - 2 * cnt_c);
+        }
+    }
+    // Metropolis test on x = alpha * D; the temporal part is in the growth
+    const int D = D6 / 6;
+    bool acc = D <= 0;
+    if (!acc) {
+        const int q = D >> 1;
+        const uint32_t T = q <= alen ? __ldg(J.Tacc + aoff + q - 1) : 0u;
+        const uint32_t rho = (uint32_t)gw * 32u + (uint32_t)lane;
+        const U4 P = philox((uint32_t)t, canon, rho >> 2, (uint32_t)inst, J.seed_lo, J.key_wacc);
+        acc = T == 0xFFFFFFFFu || word_of(P, (int)(rho & 3u)) < T;
+    }
+    const uint32_t flip = __ballot_sync(full, acc) & valid_bits(J.R, gw);
+#pragma unroll
+    for (int j = 0; j < SPL; j++) {
+        const int tau = lane * SPL + j;
+        if (tau < L) sm.S[(size_t)tau * J.zstride + idx] = s[j] ^ (C[j] & flip);
+    }
+}
+
+// A unit of time-like cluster sweeps: the whole imaginary-time ring of every
+// site stays in this block (no cluster split).
+template <int SPL>
+__device__ void run_unit_wolff(const JobDev &J, const Smem &sm, const Unit &u)
+{
+    const int nthr = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    const int Z = J.Z, n = J.n, wc = u.wc, inst = u.inst, w0 = u.w0;
+    for (int i = tid; i < Z * n * wc; i += nthr) {
+        const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
+        sm.S[(size_t)zl * J.zstride + si * wc + w] = J.state[(((size_t)inst * Z + zl) * n + si) * J.W + w0 + w];
+    }
+    {
+        const uint32_t *src = (const uint32_t *)(J.sites + (size_t)inst * n);
+        uint32_t *dst = (uint32_t *)sm.sites;
+        for (int i = tid; i < n * (int)(sizeof(SiteRec) / 4); i += nthr) dst[i] = src[i];
+    }
+    __syncthreads();
+    uint32_t *start = sm.M + (size_t)warp * SPL * 32;
+    for (int t = J.t0; t < J.t1; t++) {
+        const uint32_t Tb = __ldg(J.Tb + t);
+        const int aoff = __ldg(J.acc_off + t), alen = __ldg(J.acc_len + t);
+        for (int chi = 0; chi < J.ncol; chi++) {
+            const int c0 = J.col_ptr[chi];
+            const int nitems = (J.col_ptr[chi + 1] - c0) * wc;
+            for (int it = warp; it < nitems; it += nwarps)
+                wolff_item<SPL>(J, sm, start, inst, w0, wc, t, c0 + it / wc, it % wc, Tb, aoff, alen, lane);
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < Z * n * wc; i += nthr) {
+        const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
+        J.state[(((size_t)inst * Z + zl) * n + si) * J.W + w0 + w] = sm.S[(size_t)zl * J.zstride + si * wc + w];
+    }
+    __syncthreads();
+}
+
 template <int KIND, bool LUT>
 __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 {
@@ -636,6 +880,10 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel_one(const __grid_constant
             run_unit<SQA_KIND_PT, false>(J, sm, u);
         else if (MODE == 2)
             run_unit<SQA_KIND_SQA, true>(J, sm, u);
+        else if (MODE == 3)
+            run_unit_wolff<2>(J, sm, u);
+        else if (MODE == 4)
+            run_unit_wolff<4>(J, sm, u);
         else
             run_unit<SQA_KIND_SQA, false>(J, sm, u);
     }
@@ -643,12 +891,24 @@ __global__ void __launch_bounds__(256, 3) sweep_kernel_one(const __grid_constant
 
 // Host side of the single-job kernel: its entry for a job's path, and the
 // launch (a cluster launch when the job's units span several blocks).
-static int one_mode(const JobDev &J) { return J.kind == SQA_KIND_PT ? 0 : (J.use_lut ? 2 : 1); }
+// Modes: 0 PT, 1 SQA windows, 2 SQA tables, 3 / 4 SQA cluster moves with
+// 2 / 4 slices per lane (L <= 64 / L <= 128).
+static int one_mode(const JobDev &J)
+{
+    if (J.kind == SQA_KIND_PT) return 0;
+    if (J.move == SQA_MOVE_WOLFF) return J.Z <= 64 ? 3 : 4;
+    return J.use_lut ? 2 : 1;
+}
 
 const void *sweep_one_entry_mode(int mode)
 {
-    return mode == 0 ? (const void *)sweep_kernel_one<0>
-                     : (mode == 1 ? (const void *)sweep_kernel_one<1> : (const void *)sweep_kernel_one<2>);
+    switch (mode) {
+    case 0: return (const void *)sweep_kernel_one<0>;
+    case 1: return (const void *)sweep_kernel_one<1>;
+    case 2: return (const void *)sweep_kernel_one<2>;
+    case 3: return (const void *)sweep_kernel_one<3>;
+    default: return (const void *)sweep_kernel_one<4>;
+    }
 }
 
 const void *sweep_one_entry(const JobDev &J) { return sweep_one_entry_mode(one_mode(J)); }
@@ -671,7 +931,9 @@ cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, in
     switch (one_mode(J)) {
     case 0: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<0>, J, units, n_units, counter);
     case 1: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<1>, J, units, n_units, counter);
-    default: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<2>, J, units, n_units, counter);
+    case 2: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<2>, J, units, n_units, counter);
+    case 3: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<3>, J, units, n_units, counter);
+    default: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<4>, J, units, n_units, counter);
     }
 }
 
@@ -717,6 +979,10 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const
         const Smem sm = carve(s_job, smem_raw);
         if (s_job.kind == SQA_KIND_PT)
             run_unit<SQA_KIND_PT, false>(s_job, sm, u);
+        else if (s_job.move == SQA_MOVE_WOLFF && s_job.Z <= 64)
+            run_unit_wolff<2>(s_job, sm, u);
+        else if (s_job.move == SQA_MOVE_WOLFF)
+            run_unit_wolff<4>(s_job, sm, u);
         else if (s_job.use_lut)
             run_unit<SQA_KIND_SQA, true>(s_job, sm, u);
         else

@@ -20,7 +20,7 @@ struct SmemOffsets {
     size_t lut;    // SQA: per-site tables of threshold high halves
     size_t sites;  // SiteRec [n]
     size_t E;      // PT: energies [P][wc*32]
-    size_t M;      // PT: swap masks [P/2+1][wc]
+    size_t M;      // PT: swap masks [P/2+1][wc]; cluster moves: per-warp start masks [8][64 or 128]
     size_t total;
 };
 
@@ -32,6 +32,19 @@ SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
     size_t off = 0;
     o.S = off;
     off += (size_t)J.zr * zstride * 4;
+    if (J.kind == SQA_KIND_SQA && J.move == SQA_MOVE_WOLFF) {
+        // cluster moves: the state, the site records and, per warp, the
+        // start masks of one ring (M): no threshold rows or tables
+        o.T = o.Tq = o.lut = off;
+        off = align16(off);
+        o.sites = off;
+        off += (size_t)J.n * sizeof(SiteRec);
+        off = align16(off);
+        o.E = o.M = off;
+        off += (size_t)(256 / 32) * (J.Z <= 64 ? 64 : 128) * 4;
+        o.total = align16(off);
+        return o;
+    }
     o.T = off;
     off += (size_t)(J.kind == SQA_KIND_SQA ? J.nrow : J.zr * J.nrow) * 4;
     o.Tq = off;

@@ -23,6 +23,9 @@ constexpr uint32_t kDomSweepHi = 0xBB67AE85u;
 constexpr uint32_t kDomSweepLo = 0x3C6EF372u;
 constexpr uint32_t kDomSwap = 0xA54FF53Au;
 constexpr uint32_t kDomTree = 0x510E527Fu;
+constexpr uint32_t kDomWStart = 0x9B05688Cu;  // cluster start slice
+constexpr uint32_t kDomWBond = 0x1F83D9ABu;   // cluster bond bit-planes
+constexpr uint32_t kDomWAcc = 0x5BE0CD19u;    // cluster acceptance
 
 struct U4 {
     uint32_t x, y, z, w;

@@ -88,6 +88,13 @@ struct JobDev {
     int n_ecls;      // weight classes used (max over instances); 0 = too many distinct weights
     int csize;       // blocks per unit (a thread-block cluster when > 1)
     int zr;          // slices (SQA) or slots (PT) per block: Z / csize
+    // time-like cluster moves (SQA, move == SQA_MOVE_WOLFF)
+    int move;
+    uint32_t key_wstart, key_wbond, key_wacc;  // seed_hi ^ kDomW*
+    const uint32_t *Tb;      // [S] bond thresholds
+    const uint32_t *Tacc;    // acceptance thresholds, D/2 = 1..acc_len[t] from acc_off[t]
+    const int *acc_off;      // [S]
+    const int *acc_len;      // [S]
 };
 
 // One unit of work: the words [w0, w0+wc) of one instance of one job.
@@ -148,6 +155,13 @@ uint32_t threshold(double x);
 void sqa_tables(const double *A, const double *B, double beta, int L, int S, int dmin, int dmax,
                 std::vector<uint32_t> &T);
 void pt_tables(const double *betas, int P, int dmin, int dmax, std::vector<uint32_t> &T);
+// Time-like cluster move tables: Tb[t] the bond threshold of sweep t
+// (floor(2^32 (1 - tanh(beta A_t / L))), 0xFFFFFFFF when A_t = 0), and per
+// sweep the acceptance thresholds T(alpha_t D) for D = 2, 4, ... up to
+// L * dmax or the first zero (off[t], len[t] into Tacc).
+uint32_t bond_threshold(double beta, double A, int L);
+void wolff_tables(const double *A, const double *B, double beta, int L, int S, int dmax, std::vector<uint32_t> &Tb,
+                  std::vector<uint32_t> &Tacc, std::vector<int> &off, std::vector<int> &len);
 void swap_tables(const double *betas, int P, std::vector<uint32_t> &T, std::vector<int> &off,
                  std::vector<int> &len);
 // Uniform labelled tree from a Pruefer sequence drawn from the TREE stream:

@@ -163,6 +163,57 @@ def test_validation_before_device_work(L):
     assert L.sqa_create(C.byref(d), C.byref(h)) == pkg.SQA_ERR_UNSUPPORTED
     assert L.sqa_create(None, C.byref(h)) == pkg.SQA_ERR_INVALID
     assert L.sqa_strerror(pkg.SQA_ERR_INVALID) == b"invalid argument"
+    d, keep = _desc("sqa", "lhz", 6, J, 9, 10)
+    d.move = 2                                                # no such move
+    assert L.sqa_create(C.byref(d), C.byref(h)) == pkg.SQA_ERR_INVALID
+    d, keep = _desc("sqa", "lhz", 6, J, 9, 10, L=130)
+    d.move = 1                                                # cluster moves need L <= 128
+    assert L.sqa_create(C.byref(d), C.byref(h)) == pkg.SQA_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("emb,N,S,Ls,beta", [("me", 8, 40, 64, 10 / 3), ("lhz", 6, 30, 16, 1.0)])
+def test_cluster_move_tables_equal_oracle(L, emb, N, S, Ls, beta):
+    """Bond thresholds and per-sweep acceptance rows, built by the library,
+    equal the oracle's bond_threshold and threshold(alpha * D), bit for bit;
+    each row ends where the threshold reaches 0 or at L * dmax."""
+    J = W.random_instances(N, 2, 3)
+    pen = 6 if emb == "me" else 9
+    A, B = O.linear_schedule(S)
+    A = A.copy()
+    A[-3:] = 0.0                                  # infinite Jperp: bonds always join
+    d, keep = _desc("sqa", emb, N, J, pen, S, L=Ls, beta=beta, A=A, B=B)
+    d.move = 1
+    n = C.c_int64()
+    assert L.sqa_plan_wolff_tables(C.byref(d), None, None, None, None, 0, C.byref(n)) == 0
+    Tb = np.zeros(S, np.uint32)
+    off = np.zeros(S, np.int32)
+    ln = np.zeros(S, np.int32)
+    Tacc = np.zeros(max(n.value, 1), np.uint32)
+    assert L.sqa_plan_wolff_tables(C.byref(d), Tb.ctypes.data, off.ctypes.data, ln.ctypes.data, Tacc.ctypes.data,
+                                   len(Tacc), C.byref(n)) == 0
+    dmin, dmax = C.c_int32(), C.c_int32()
+    assert L.sqa_plan_tables(C.byref(d), None, 0, C.byref(dmin), C.byref(dmax)) == 0
+    for t in range(S):
+        assert Tb[t] == O.bond_threshold(beta, A[t], Ls)
+        alpha = beta * B[t] / Ls
+        row = Tacc[off[t]:off[t] + ln[t]]
+        want = [O.threshold(alpha * D) for D in range(2, 2 * ln[t] + 1, 2)]
+        assert np.array_equal(row, np.array(want, np.uint32))
+        # the row stops at the first zero or at the largest cluster change
+        if ln[t] < Ls * dmax.value // 2:
+            assert O.threshold(alpha * 2 * (ln[t] + 1)) == 0
+    assert Tb[-1] == 0xFFFFFFFF
+
+
+def test_cluster_move_device_bytes(L):
+    """The admission estimate of a cluster-move job counts its own tables
+    (bond thresholds, per-sweep acceptance rows) instead of the single-spin
+    threshold table."""
+    J = W.random_instances(8, 3, 1)
+    kw = dict(embedding="me", N=8, J=J, penalty=6, sweeps=200, R=64, L=64, beta=10 / 3)
+    metro = pkg.plan_device_bytes(**kw)
+    wolff = pkg.plan_device_bytes(move="wolff", **kw)
+    assert metro > 0 and wolff > 0 and wolff != metro
 
 
 def test_no_device_is_reported():
