@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--pt-sweeps", type=int, default=100_000)
     ap.add_argument("--ragged-sweeps", type=int, default=10_000)
     ap.add_argument("--pt-instances", type=int, default=256)
+    ap.add_argument("--wolff-sweeps", type=int, default=2000)
+    ap.add_argument("--wolff-only", action="store_true",
+                    help="time only the cluster-move workload (a small case for profiling with --instances)")
     ap.add_argument("--pt-only", choices=["me", "lhz"],
                     help="time only the PT workload on this embedding (a small case for profiling)")
     ap.add_argument("--no-serving", action="store_true")
@@ -244,8 +247,32 @@ def extra_workloads(pkg, stream, args):
     for h in hs:
         h.close()
     out.update(pt_workloads(pkg, stream, args, ("me", "lhz")))
+    out["wolff_me"] = wolff_workload(pkg, stream, args)
     if not args.no_serving:
         out["serving"] = [serving_workload(pkg, args.capacity, load, args.serving_jobs) for load in (0.5, 0.8, 0.95)]
+    return out
+
+
+def wolff_workload(pkg, stream, args):
+    """The benchmark's ME K_8 anneal (1024 instances x 256 replicas, L = 64)
+    with one time-like cluster move per (site, replica) per sweep instead of
+    single-spin sweeps.  Reported per (site, slice, replica) per sweep, the
+    unit of the single-spin attempts, and per cluster move."""
+    sp = stream.cuda_stream
+    cfg = W.me_n8_batch_config(n_inst=args.instances, sweeps=args.wolff_sweeps)
+    kw = dict(embedding="me", N=cfg["N"], J=cfg["J"], penalty=cfg["penalty"], R=cfg["R"], seed=cfg["seed"],
+              L=cfg["L"], beta=cfg["beta"], move="wolff")
+    w = pkg.Handle(sweeps=20, **kw)
+    w.run(stream=sp)
+    stream.synchronize()
+    w.close()
+    h = pkg.Handle(sweeps=args.wolff_sweeps, **kw)
+    spin_slices = h.info["attempts_per_sweep"] * args.wolff_sweeps
+    moves = spin_slices // cfg["L"]
+    t = timed(stream, lambda: h.run(stream=sp))
+    out = {"workload": cfg["name"] + ", time-like cluster moves", "value": spin_slices / t,
+           "unit": "spin-slice updates/s", "cluster_moves_per_s": moves / t, "seconds": t, "launch": h.launch()}
+    h.close()
     return out
 
 
@@ -385,6 +412,11 @@ def main():
         res = pt_workloads(pkg, stream, args, (args.pt_only,))
         if rank == 0:
             print(json.dumps({"pt_only": res}))
+        return
+    if args.wolff_only:
+        res = wolff_workload(pkg, stream, args)
+        if rank == 0:
+            print(json.dumps({"wolff_only": res}))
         return
     N, R, L, S, I = cfg["N"], cfg["R"], cfg["L"], cfg["sweeps"], cfg["J"].shape[0]
     h = pkg.Handle(embedding="me", N=N, J=cfg["J"], penalty=cfg["penalty"], sweeps=S, R=R,

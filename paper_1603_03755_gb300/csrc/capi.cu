@@ -127,7 +127,11 @@ void free_all(sqa_handle *h, cudaStream_t s = 0)
 int zstride_for(const JobDev &J, int wc)
 {
     int zs = J.n * wc;
-    if (J.kind == SQA_KIND_SQA) {
+    if (J.kind == SQA_KIND_SQA && J.move == SQA_MOVE_WOLFF) {
+        // cluster moves: a warp reads 32 consecutive rows, on distinct banks
+        // when the row stride is odd
+        if (zs % 2 == 0) zs++;
+    } else if (J.kind == SQA_KIND_SQA) {
         if (wc % 2 == 0) {
             while ((2 * zs) % 32 != wc % 32) zs++;
         } else {
