@@ -66,7 +66,10 @@ typedef enum {
     SQA_DECODE_ME_MV = 0,     /* ME majority vote per chain (Eq. 4); ties -> hub spin */
     SQA_DECODE_LHZ_TREES = 1, /* LHZ majority vote over n_trees random trees (Eq. 5) */
     SQA_DECODE_LHZ_STAR = 2,  /* LHZ star tree q_i = q_{0,i} (Eq. 11) */
-    SQA_DECODE_LHZ_CHAIN = 3  /* LHZ chain tree q_i = prod_{m<i} q_{m,m+1} (Eq. 10) */
+    SQA_DECODE_LHZ_CHAIN = 3, /* LHZ chain tree q_i = prod_{m<i} q_{m,m+1} (Eq. 10) */
+    SQA_DECODE_LHZ_MWD = 4    /* LHZ minimum-weight decoding (Sec. IV A), exact by enumeration, N <= 24:
+                                 the logical state whose pair products disagree with the fewest pair
+                                 spins; q_{N-1} = +1, ties to the first state in binary order */
 } sqa_decode_method;
 
 /* Problem and program description.  All pointers are host pointers; the

@@ -90,6 +90,7 @@ def _declare(L):
         "orc_star_tree": (None, [i32, _i32p]), "orc_chain_tree": (None, [i32, _i32p]),
         "orc_lhz_tree_decode": (None, [i32, _i32p, _i8p, _i8p]),
         "orc_lhz_vote_decode": (None, [i32, i32, _i32p, _i8p, _i8p]),
+        "orc_lhz_mwd_decode": (None, [i32, _i8p, _i8p]),
         "orc_logical_energy": (i64, [i32, _i32p, _i8p]),
         "orc_ground_energy": (i64, [i32, _i32p, _i8p]),
     }
@@ -354,6 +355,13 @@ def lhz_tree_decode(N: int, parent, phys) -> np.ndarray:
     out = np.zeros(N, np.int8)
     lib().orc_lhz_tree_decode(N, np.ascontiguousarray(parent, np.int32),
                               np.ascontiguousarray(phys, np.int8), out)
+    return out
+
+
+def lhz_mwd_decode(N: int, phys) -> np.ndarray:
+    """Minimum-weight decoding (exact, by enumeration; q_{N-1} = +1)."""
+    out = np.zeros(N, np.int8)
+    lib().orc_lhz_mwd_decode(N, np.ascontiguousarray(phys, np.int8), out)
     return out
 
 

@@ -132,6 +132,28 @@ void orc_lhz_tree_decode(int32_t N, const int32_t *parent, const int8_t *phys, i
     }
 }
 
+void orc_lhz_mwd_decode(int32_t N, const int8_t *phys, int8_t *logical)
+{
+    int8_t *q = (int8_t *)malloc((size_t)N);
+    int64_t best = 0;
+    int have = 0;
+    uint64_t count = (uint64_t)1 << (N - 1);
+    for (uint64_t x = 0; x < count; x++) {
+        for (int32_t i = 0; i < N - 1; i++) q[i] = ((x >> i) & 1) ? -1 : 1;
+        q[N - 1] = 1;
+        /* agreement of the pair spins with the pair products */
+        int64_t score = 0;
+        for (int32_t i = 0; i < N; i++)
+            for (int32_t j = i + 1; j < N; j++) score += (int64_t)phys[orc_lhz_index(N, i, j)] * q[i] * q[j];
+        if (!have || score > best) {
+            best = score;
+            have = 1;
+            for (int32_t i = 0; i < N; i++) logical[i] = q[i];
+        }
+    }
+    free(q);
+}
+
 void orc_lhz_vote_decode(int32_t N, int32_t n_trees, const int32_t *parents,
                          const int8_t *phys, int8_t *logical)
 {

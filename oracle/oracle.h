@@ -154,6 +154,11 @@ void orc_prufer_tree(int32_t N, uint64_t seed, int32_t inst, int32_t tree, int32
 void orc_star_tree(int32_t N, int32_t *parent);
 void orc_chain_tree(int32_t N, int32_t *parent);
 void orc_lhz_tree_decode(int32_t N, const int32_t *parent, const int8_t *phys, int8_t *logical);
+/* Minimum-weight decoding of an LHZ readout (Sec. IV A): the logical state
+ * whose pair products q_i q_j disagree with the fewest pair spins of phys,
+ * i.e. the ground state of -sum_{i<j} s_ij q_i q_j.  q_{N-1} = +1; ties go to
+ * the first state in binary order (bit i of x set <-> q_i = -1). */
+void orc_lhz_mwd_decode(int32_t N, const int8_t *phys, int8_t *logical);
 void orc_lhz_vote_decode(int32_t N, int32_t n_trees, const int32_t *parents,
                          const int8_t *phys, int8_t *logical);
 int64_t orc_logical_energy(int32_t N, const int32_t *J, const int8_t *s);

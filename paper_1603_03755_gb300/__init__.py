@@ -21,7 +21,7 @@ SQA_ERR_CUDA, SQA_ERR_TIMEOUT, SQA_ERR_NO_DEVICE, SQA_ERR_BUSY = -4, -5, -6, -7
 EMB = {"me": 0, "lhz": 1}
 KIND = {"sqa": 0, "pt": 1}
 MOVE = {"metropolis": 0, "wolff": 1}
-DECODE = {"me_mv": 0, "lhz_trees": 1, "lhz_star": 2, "lhz_chain": 3}
+DECODE = {"me_mv": 0, "lhz_trees": 1, "lhz_star": 2, "lhz_chain": 3, "lhz_mwd": 4}
 
 LIB_PATH = _build.LIB
 

@@ -853,8 +853,10 @@ sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *lo
     if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
     const bool me = h->emb == SQA_EMB_ME_CHIMERA;
     if (me != (method == SQA_DECODE_ME_MV) ||
-        (method < SQA_DECODE_ME_MV || method > SQA_DECODE_LHZ_CHAIN))
+        (method < SQA_DECODE_ME_MV || method > SQA_DECODE_LHZ_MWD))
         return set_error("decode method does not match the embedding"), SQA_ERR_INVALID;
+    if (method == SQA_DECODE_LHZ_MWD && h->N > 24)
+        return set_error("minimum-weight decoding enumerates 2^(N-1) states: N <= 24"), SQA_ERR_UNSUPPORTED;
     if (method == SQA_DECODE_LHZ_TREES) {
         if (n_trees == 0) {
             n_trees = (h->N + 3) / 4 + 1;
@@ -866,7 +868,7 @@ sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *lo
     }
     cudaStream_t s = (cudaStream_t)stream;
     sqa_status st;
-    if (!me && (st = decode_trees(h, method, n_trees)) != SQA_OK) return st;
+    if (!me && method != SQA_DECODE_LHZ_MWD && (st = decode_trees(h, method, n_trees)) != SQA_OK) return st;
     const size_t nrep = (size_t)h->I * h->R;
     DecodeArgs D{};
     D.method = method;

@@ -1054,6 +1054,37 @@ __global__ void decode_kernel(JobDev J, DecodeArgs D)
                 for (int k = 0; k < len; k++) sum += sig(D.chain[l * len + k]);
                 q[l] = (int8_t)(sum > 0 ? 1 : (sum < 0 ? -1 : sig(D.chain[l * len])));
             }
+        } else if (D.method == SQA_DECODE_LHZ_MWD) {
+            // minimum-weight decoding: walk the 2^(N-1) assignments with
+            // q_{N-1} = +1 in Gray-code order; M counts the pair spins that
+            // disagree with q_a q_b (bit a of X set <-> q_a = -1, bit b of
+            // G[a] set <-> pair spin (a,b) is -1).  Flipping bit k toggles
+            // the N-1 pairs at k.
+            uint32_t G[24];
+            for (int a = 0; a < N; a++) {
+                uint32_t g = 0u;
+                for (int c = 0; c < N; c++)
+                    if (c != a && sig(D.pair[a * N + c]) < 0) g |= 1u << c;
+                G[a] = g;
+            }
+            const uint32_t all = N == 32 ? 0xFFFFFFFFu : ((1u << N) - 1u);
+            int M = 0;
+            for (int a = 0; a < N; a++) M += __popc(G[a] & ~((2u << a) - 1u));
+            uint32_t X = 0u, bestX = 0u;
+            int bestM = M;
+            const uint32_t steps = 1u << (N - 1);
+            for (uint32_t k2 = 1; k2 < steps; k2++) {
+                const int k = __ffs(k2) - 1;
+                const uint32_t xk = (X >> k) & 1u ? all : 0u;
+                const int mis = __popc((G[k] ^ X ^ xk) & all & ~(1u << k));
+                M += (N - 1) - 2 * mis;
+                X ^= 1u << k;
+                if (M < bestM || (M == bestM && X < bestX)) {
+                    bestM = M;
+                    bestX = X;
+                }
+            }
+            for (int l = 0; l < N; l++) q[l] = (int8_t)((bestX >> l) & 1u ? -1 : 1);
         } else {
             int votes[kMaxN];
             int8_t first[kMaxN];

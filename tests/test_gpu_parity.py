@@ -174,13 +174,16 @@ def _oracle_decode(pb, method, phys, seed, inst, n_trees):
         return O.lhz_tree_decode(N, O.star_tree(N), phys)
     if method == "lhz_chain":
         return O.lhz_tree_decode(N, O.chain_tree(N), phys)
+    if method == "lhz_mwd":
+        return O.lhz_mwd_decode(N, phys)
     trees = np.stack([O.prufer_tree(N, seed, inst, t) for t in range(n_trees)])
     return O.lhz_vote_decode(N, trees, phys)
 
 
 @pytest.mark.parametrize("emb,method,N", [("me", "me_mv", 8), ("me", "me_mv", 12),
                                           ("lhz", "lhz_trees", 8), ("lhz", "lhz_star", 6),
-                                          ("lhz", "lhz_chain", 7)])
+                                          ("lhz", "lhz_chain", 7), ("lhz", "lhz_mwd", 8),
+                                          ("lhz", "lhz_mwd", 11)])
 def test_decode_parity(emb, method, N):
     I, R, L, S = 3, 70, 8, 30
     pen = 6 if emb == "me" else 9
@@ -201,6 +204,29 @@ def test_decode_parity(emb, method, N):
             assert energy[i, r] == e
             cnt += e == eg[i]
         assert succ[i] == cnt
+
+
+def test_mwd_decode_of_pt_readouts_k16():
+    """Minimum-weight decoding of PT's coldest slot on LHZ K_16 (2^15 states
+    per readout), sampled replicas against the oracle; N > 24 is refused."""
+    N, R, S = 16, 64, 40
+    J = W.random_instances(N, 2, 88)
+    betas = W.geometric_ladder(6, 5.0, 0.5)
+    h = pkg.Handle(embedding="lhz", N=N, J=J, penalty=9, sweeps=S, R=R, seed=88, kind="pt", betas=betas,
+                   swap_every=1)
+    h.run(stream=0)
+    phys = pkg.unpack_words(h.readout(stream=0), R)
+    logical, energy, _ = h.decode("lhz_mwd", 0, stream=0)
+    for i in range(2):
+        for r in (0, 1, 17, 40, 63):
+            assert np.array_equal(logical[i, r], O.lhz_mwd_decode(N, phys[i, :, r])), (i, r)
+    h.close()
+    J25 = W.random_instances(25, 1, 1)
+    h = pkg.Handle(embedding="lhz", N=25, J=J25, penalty=9, sweeps=2, R=32, seed=1, L=4, beta=1.0)
+    h.run(stream=0)
+    with pytest.raises(pkg.SQAError):
+        h.decode("lhz_mwd", 0, stream=0)
+    h.close()
 
 
 @pytest.mark.parametrize("N", [2, 3, 5, 8, 11, 16])

@@ -153,3 +153,51 @@ def test_logical_energy_definition():
     s = np.array([1, -1, -1, 1, -1], np.int8)
     e = sum(int(J[O.lhz_index(N, i, j)]) * s[i] * s[j] for i in range(N) for j in range(i + 1, N))
     assert O.logical_energy(N, J, s) == e
+
+
+# ---------------------------------------------------------------------------
+# Minimum-weight decoding (Sec. IV A): the constraint-satisfying state nearest
+# in Hamming distance to the readout, returned as the logical state with
+# q_{N-1} = +1 (the Z2 partner is the same physical state).
+# ---------------------------------------------------------------------------
+
+def _all_logical(N):
+    x = np.arange(2 ** (N - 1))
+    q = np.where((x[:, None] >> np.arange(N - 1)[None, :]) & 1, -1, 1)
+    return np.concatenate([q, np.ones((len(x), 1), int)], axis=1)      # binary order, q_{N-1} = +1
+
+
+@pytest.mark.parametrize("N", [3, 5, 7, 9])
+def test_mwd_is_the_nearest_valid_state(N):
+    """Brute force over every logical state: the decoded state's pair
+    products differ from the readout in the fewest pair spins, and among
+    equally near states it is the first in binary order."""
+    pb = O.Problem("lhz", N, W.random_couplings(N, 6), 3)
+    rng = np.random.default_rng(N)
+    Q = _all_logical(N)
+    iu = np.triu_indices(N, 1)
+    for _ in range(40):
+        phys = _random_phys(pb, rng)
+        pairs = np.array([phys[O.lhz_index(N, i, j)] for i, j in zip(*iu)])
+        dist = ((Q[:, iu[0]] * Q[:, iu[1]]) != pairs[None, :]).sum(axis=1)
+        want = Q[int(np.argmin(dist))]                  # argmin takes the first minimum
+        assert np.array_equal(O.lhz_mwd_decode(N, phys), want)
+
+
+@pytest.mark.parametrize("N", [5, 8, 12])
+def test_mwd_corrects_flipped_pair_spins(N):
+    """Valid states decode to themselves; with fewer than (N-1)/2 flipped pair
+    spins (two valid states differ in at least N-1 pair spins) the original
+    logical state comes back."""
+    pb = O.Problem("lhz", N, W.random_couplings(N, 2), 3)
+    rng = np.random.default_rng(3 * N)
+    K = N * (N - 1) // 2
+    for _ in range(20):
+        s = np.where(rng.random(N) < 0.5, -1, 1).astype(np.int8)
+        gauge = s * s[N - 1]
+        phys = pb.embed(s)
+        assert np.array_equal(O.lhz_mwd_decode(N, phys), gauge)
+        bad = phys.copy()
+        flips = rng.choice(K, size=(N - 2) // 2, replace=False)
+        bad[flips] *= -1
+        assert np.array_equal(O.lhz_mwd_decode(N, bad), gauge)

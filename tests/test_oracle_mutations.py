@@ -74,8 +74,15 @@ MUTANTS = [
      "D += orc_flip_delta(pb, s + (int64_t)tau0 * n * R, R, rho, site);"),
     ("ME majority-vote tie rule", "decode.c", "logical[i] = phys[hub[i]];", "logical[i] = 1;"),
     ("LHZ tree vote tie rule", "decode.c", "(sum < 0 ? -1 : tmp[i])", "(sum < 0 ? -1 : 1)"),
+    ("minimum-weight decoding keeps the last of equally near states", "decode.c",
+     "if (!have || score > best) {\n            best = score;\n            have = 1;\n            for (int32_t i = 0; i < N; i++) logical[i] = q[i];",
+     "if (!have || score >= best) {\n            best = score;\n            have = 1;\n            for (int32_t i = 0; i < N; i++) logical[i] = q[i];"),
+    ("minimum-weight decoding maximises disagreement", "decode.c",
+     "score += (int64_t)phys[orc_lhz_index(N, i, j)] * q[i] * q[j];",
+     "score -= (int64_t)phys[orc_lhz_index(N, i, j)] * q[i] * q[j];"),
     ("ground-state enumeration half short", "decode.c",
-     "uint64_t count = (uint64_t)1 << (N - 1);", "uint64_t count = (uint64_t)1 << (N - 2);"),
+     "int have = 0;\n    uint64_t count = (uint64_t)1 << (N - 1);\n    for (uint64_t x = 0; x < count; x++) {\n        for (int32_t i = 0; i < N - 1; i++) s[i]",
+     "int have = 0;\n    uint64_t count = (uint64_t)1 << (N - 2);\n    for (uint64_t x = 0; x < count; x++) {\n        for (int32_t i = 0; i < N - 1; i++) s[i]"),
 ]
 
 
