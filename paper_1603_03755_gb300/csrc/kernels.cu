@@ -286,45 +286,53 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
     const int gw = w0 + w;
     const uint32_t slot = (uint32_t)(sr.canon * J.Z + z);
     const uint32_t g0 = (uint32_t)gw * 4u;
+    // the four Philox blocks first (independent chains the scheduler can
+    // interleave), then the 32 compares; ties are fixed after all of them
+    U4 Ar[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) Ar[r] = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.khi);
     uint32_t rej = 0u;  // bit 8r + j: replica j + 8r rejects
+    bool tie = false;
 #pragma unroll
     for (int r = 3; r >= 0; r--) {
-        const U4 Ar = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.khi);
-        uint32_t hi = 0u;
-        bool tie = false;
 #pragma unroll
         for (int j = 7; j >= 0; j--) {
             const int32_t q = Q[__byte_perm(code[j], 0u, 0x4440u + (uint32_t)r)];
-            const uint32_t aw = word_of(Ar, j >> 1);
+            const uint32_t aw = word_of(Ar[r], j >> 1);
             // the replica's 16 high uniform bits at the top of x (an odd
             // replica's low neighbour bits below them do not change x >= q)
             const uint32_t x = (j & 1) ? aw : (aw << 16);
-            const uint32_t d = sub_carry_into(x, (uint32_t)q, hi);  // append the reject bit
+            const uint32_t d = sub_carry_into(x, (uint32_t)q, rej);  // append the reject bit
             tie |= d < 0x10000u;
         }
-        if (tie) {
-            // high halves equal (probability 2^-16): draw the low half and
-            // compare the whole uniform with the whole threshold
-            const U4 Br = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.klo);
+    }
+    if (tie) {
+        // high halves equal (probability 2^-16 per replica): redraw the
+        // block, draw the low halves and compare whole uniforms with whole
+        // thresholds (the blocks are recomputed so they need not stay live)
+#pragma unroll 1
+        for (int r = 0; r < 4; r++) {
+            const U4 A2 = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.khi);
+            const U4 B2 = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.klo);
 #pragma unroll
-            for (int j = 7; j >= 0; j--) {
+            for (int j = 0; j < 8; j++) {
                 const uint32_t c = __byte_perm(code[j], 0u, 0x4440u + (uint32_t)r);
-                const uint32_t aw = word_of(Ar, j >> 1);
+                const uint32_t aw = word_of(A2, j >> 1);
                 const uint32_t x = (j & 1) ? aw : (aw << 16);
                 const uint32_t d = x - (uint32_t)Q[c];
                 if (d < 0x10000u) {
                     const uint32_t sh = 16u * (uint32_t)(j & 1);
-                    uint32_t u = ((aw >> sh) & 0xFFFFu) << 16 | ((word_of(Br, j >> 1) >> sh) & 0xFFFFu);
+                    uint32_t u = ((aw >> sh) & 0xFFFFu) << 16 | ((word_of(B2, j >> 1) >> sh) & 0xFFFFu);
                     u = u < 0xFFFFFFFEu ? u : 0xFFFFFFFEu;
                     const uint32_t T = Tfull[LUT ? full_index<KIND>(sr, c) : sr.base + (int)c];
+                    const uint32_t bit = 1u << (8 * r + j);
                     if (u < T)
-                        hi &= ~(1u << j);
+                        rej &= ~bit;
                     else
-                        hi |= 1u << j;
+                        rej |= bit;
                 }
             }
         }
-        rej = (rej << 8) | hi;
     }
     row[idx] = s ^ (~rej & valid_bits(J.R, gw));
 }
