@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--pt-only", choices=["me", "lhz"],
                     help="time only the PT workload on this embedding (a small case for profiling)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-only", type=float, default=0.0, metavar="CAPACITY",
+                    help="run only the serving stream, offered loads relative to CAPACITY attempts/s")
     ap.add_argument("--serving-jobs", type=int, default=200)
     return ap.parse_args()
 
@@ -412,6 +414,11 @@ def main():
         res = pt_workloads(pkg, stream, args, (args.pt_only,))
         if rank == 0:
             print(json.dumps({"pt_only": res}))
+        return
+    if args.serving_only:
+        res = [serving_workload(pkg, args.serving_only, load, args.serving_jobs) for load in (0.5, 0.8, 0.95)]
+        if rank == 0:
+            print(json.dumps({"serving_only": res}))
         return
     if args.wolff_only:
         res = wolff_workload(pkg, stream, args)

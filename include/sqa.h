@@ -127,7 +127,7 @@ sqa_status sqa_get_info(const sqa_handle *h, sqa_info *out);
  * depend on them).  words_per_unit: 32-replica words one unit holds
  * (0 = automatic).  use_table: SQA threshold lookup through per-site code
  * tables (1), byte-wise index windows (0), or automatic (-1); PT always uses
- * windows.  cluster: blocks per unit, 1, 2, 4 or 8 (0 = automatic); with
+ * windows.  cluster: blocks per unit, 1, 2, 4, 8 or 16 (0 = automatic); with
  * C > 1 a thread-block cluster sweeps one unit, each block holding Z/C
  * consecutive slices (SQA, C must divide L/2) or slots (PT, C must divide
  * P).  Fails with SQA_ERR_UNSUPPORTED, leaving the shape unchanged, when the
@@ -222,7 +222,7 @@ sqa_status sqa_batch_autotune(sqa_batch *b, int32_t n_trial, void *stream, int32
                               double *attempts_per_s);
 void sqa_batch_destroy(sqa_batch *b);
 /* Times h's sweep kernel in every launch shape that fits (cluster size 1, 2,
- * 4, 8; table or window lookup; words per unit W, ceil(W/2), ..., 1) on
+ * 4, 8, 16; table or window lookup; words per unit W, ceil(W/2), ..., 1) on
  * n_trial sweeps from sweep 0 and keeps the fastest (as sqa_tune).  h's
  * spins are saved and restored.  Synchronous; the out pointers (may be
  * NULL) receive the choice and its trial rate in attempts/s. */

@@ -266,7 +266,7 @@ sqa_status sqa_autotune(sqa_handle *h, int32_t n_trial, void *stream, int32_t *w
         double t;
     } best{0, -1, 0, -1};
     sqa_status st = SQA_OK;
-    for (int C = 1; C <= 8 && st == SQA_OK; C *= 2)
+    for (int C = 1; C <= 16 && st == SQA_OK; C *= 2)
         for (int lut : {1, 0}) {
             if (h->kind == SQA_KIND_PT && lut == 0) continue;  // PT has one lookup form
             const int mode = h->kind == SQA_KIND_PT ? -1 : lut;

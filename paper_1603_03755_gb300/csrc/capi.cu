@@ -71,6 +71,12 @@ sqa_status device_ready()
             limit = std::min(limit, (int)prop.sharedMemPerBlockOptin - (int)fk.sharedSizeBytes);
         }
         for (const void *k : ks) SQA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+        // single-job kernels may run 16-block clusters (one unit over 16 SMs'
+        // worth of blocks); where the device refuses, clusters stop at 8
+        for (int m = 0; m < 5; m++)
+            if (cudaFuncSetAttribute(sweep_one_entry_mode(m), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess)
+                cudaGetLastError();
         g_num_sms = prop.multiProcessorCount;
         g_smem_limit = limit;
     }
@@ -172,6 +178,8 @@ sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> 
         double score = -1;
         int C = 0, wc = 0, lut = 0;
     } best;
+    // automatic plans stop at 8-block clusters: wider ones are hard to place
+    // beside other work (16 is available through sqa_tune)
     const int cmax = c_forced > 0 ? c_forced : 8;
     const bool wolff = J.kind == SQA_KIND_SQA && J.move == SQA_MOVE_WOLFF;
     for (int C = c_forced > 0 ? c_forced : 1; C <= cmax; C *= 2) {
@@ -646,7 +654,7 @@ sqa_status sqa_get_info(const sqa_handle *h, sqa_info *o)
 
 sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, int32_t cluster)
 {
-    if (!h || words_per_unit < 0 || use_table < -1 || use_table > 1 || cluster < 0 || cluster > 8 ||
+    if (!h || words_per_unit < 0 || use_table < -1 || use_table > 1 || cluster < 0 || cluster > 16 ||
         (cluster & (cluster - 1)))
         return set_error("tune arguments"), SQA_ERR_INVALID;
     if (use_table == 0 && h->window_limit_exceeded) return set_error("window mode cannot hold this problem"), SQA_ERR_UNSUPPORTED;

@@ -280,7 +280,8 @@ def test_launch_shapes_give_the_oracle_bits(emb, use_table, wc):
 
 @pytest.mark.parametrize("kind,emb,N,Z,R,C", [("sqa", "lhz", 8, 16, 64, 2), ("sqa", "me", 12, 16, 40, 4),
                                               ("sqa", "lhz", 6, 16, 33, 8), ("pt", "me", 8, 8, 64, 2),
-                                              ("pt", "lhz", 7, 8, 32, 4), ("pt", "me", 5, 16, 40, 8)])
+                                              ("pt", "lhz", 7, 8, 32, 4), ("pt", "me", 5, 16, 40, 8),
+                                              ("sqa", "lhz", 6, 32, 40, 16), ("pt", "me", 6, 16, 33, 16)])
 def test_cluster_split_gives_the_oracle_bits(kind, emb, N, Z, R, C):
     """A thread-block cluster sweeping one unit, each block holding Z/C slices or
     slots (temporal neighbours and swap partners across blocks)."""
