@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--ragged-sweeps", type=int, default=10_000)
     ap.add_argument("--pt-instances", type=int, default=256)
     ap.add_argument("--wolff-sweeps", type=int, default=2000)
+    ap.add_argument("--scan-sweeps", type=int, default=2000)
     ap.add_argument("--wolff-only", action="store_true",
                     help="time only the cluster-move workload (a small case for profiling with --instances)")
     ap.add_argument("--pt-only", choices=["me", "lhz"],
@@ -250,6 +251,7 @@ def extra_workloads(pkg, stream, args):
         h.close()
     out.update(pt_workloads(pkg, stream, args, ("me", "lhz")))
     out["wolff_me"] = wolff_workload(pkg, stream, args)
+    out["penalty_scans"] = scan_workloads(pkg, stream, args)
     if not args.no_serving:
         out["serving"] = [serving_workload(pkg, args.capacity, load, args.serving_jobs) for load in (0.5, 0.8, 0.95)]
     return out
@@ -275,6 +277,37 @@ def wolff_workload(pkg, stream, args):
     out = {"workload": cfg["name"] + ", time-like cluster moves", "value": spin_slices / t,
            "unit": "spin-slice updates/s", "cluster_moves_per_s": moves / t, "seconds": t, "launch": h.launch()}
     h.close()
+    return out
+
+
+def scan_workloads(pkg, stream, args):
+    """Penalty scans of 32 K_8 instances (J in {+-1, +-2, +-3}) at penalties
+    1, 2, 3, 4, 6, 8, 10, 12, each scan one batch launch: SQA (L = 64, beta = 1,
+    256 readouts per instance and penalty) for the optimal penalty, and PT on
+    the paper's ladder (32 temperatures, beta 20 down to 0.1, readouts from
+    beta = 20) for the critical penalty."""
+    from paper_1603_03755_gb300.scan import penalty_scan
+    sp = stream.cuda_stream
+    pens = [1, 2, 3, 4, 6, 8, 10, 12]
+    J = W.random_instances(8, 32, 5)
+    out = {}
+    for emb in ("me", "lhz"):
+        for kind in ("sqa", "pt"):
+            anneal = (dict(L=64, beta=1.0) if kind == "sqa"
+                      else dict(betas=W.paper_beta_ladder(32, 20.0, 0.1), swap_every=1))
+            t0 = time.perf_counter()
+            res = penalty_scan(embedding=emb, N=8, J=J, penalties=pens, R=256, sweeps=args.scan_sweeps, seed=5,
+                               kind=kind, stream=sp, **anneal)
+            dt = time.perf_counter() - t0
+            best = res.success.max(axis=0)
+            out[f"{kind}_{emb}"] = {
+                "sweeps": args.scan_sweeps, "penalties": pens, "seconds_end_to_end": dt,
+                "attempts_per_s_end_to_end": res.attempts / dt,
+                "mean_success_at_optimal": float(best.mean()),
+                "mean_optimal_penalty": float(res.optimal.mean()),
+                "mean_critical_penalty": (float(np.nanmean(res.critical)) if np.isfinite(res.critical).any()
+                                          else None),
+                "instances_reaching_half": int(np.isfinite(res.critical).sum())}
     return out
 
 
