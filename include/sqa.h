@@ -67,9 +67,11 @@ typedef enum {
     SQA_DECODE_LHZ_TREES = 1, /* LHZ majority vote over n_trees random trees (Eq. 5) */
     SQA_DECODE_LHZ_STAR = 2,  /* LHZ star tree q_i = q_{0,i} (Eq. 11) */
     SQA_DECODE_LHZ_CHAIN = 3, /* LHZ chain tree q_i = prod_{m<i} q_{m,m+1} (Eq. 10) */
-    SQA_DECODE_LHZ_MWD = 4    /* LHZ minimum-weight decoding (Sec. IV A), exact by enumeration, N <= 24:
+    SQA_DECODE_LHZ_MWD = 4,   /* LHZ minimum-weight decoding (Sec. IV A), exact by enumeration, N <= 24:
                                  the logical state whose pair products disagree with the fewest pair
                                  spins; q_{N-1} = +1, ties to the first state in binary order */
+    SQA_DECODE_LHZ_BP = 5     /* LHZ belief propagation (Sec. IV, App. C), N <= 32, error rate 0.2 and
+                                 10 iterations (sqa_decode_bp for others), read out by random tree 0 */
 } sqa_decode_method;
 
 /* Problem and program description.  All pointers are host pointers; the
@@ -198,6 +200,17 @@ sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, i
  * so calls that overlap on the GPU race with each other. */
 sqa_status sqa_ground_energy_noalloc(int32_t N, int32_t n_instances, const int32_t *J_dev,
                                      int64_t *e_dev, void *stream);
+
+/* Belief-propagation decoding of an LHZ handle's readouts (Sec. IV, App. C):
+ * pair values start at the readout's pair spins s and are updated
+ * `iterations` times, all pairs at once, p_ij <- sign(L0 s_ij + L2 sum_l
+ * p_il p_lj) over the N-2 third spins l (ties keep p_ij), with
+ * L0 = ln((1-e)/e) and L2 = ln(((1-e)^2 + e^2) / (2 e (1-e))) for error rate
+ * e in (0, 1/2]; random tree 0 of the instance then reads the logical
+ * state.  N <= 32.  Outputs and streams as sqa_decode. */
+sqa_status sqa_decode_bp(sqa_handle *h, double error_rate, int32_t iterations, int8_t *logical_out,
+                         int64_t *energy_out, const int64_t *e_ground, int32_t *success_out,
+                         int32_t out_is_device, void *stream);
 
 /* ---- reusable batches (CUDA graph) and the launch-shape autotuner ---- */
 

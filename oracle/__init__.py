@@ -91,6 +91,7 @@ def _declare(L):
         "orc_lhz_tree_decode": (None, [i32, _i32p, _i8p, _i8p]),
         "orc_lhz_vote_decode": (None, [i32, i32, _i32p, _i8p, _i8p]),
         "orc_lhz_mwd_decode": (None, [i32, _i8p, _i8p]),
+        "orc_lhz_bp_decode": (None, [i32, _i8p, dbl, i32, _i32p, _i8p]),
         "orc_logical_energy": (i64, [i32, _i32p, _i8p]),
         "orc_ground_energy": (i64, [i32, _i32p, _i8p]),
     }
@@ -362,6 +363,15 @@ def lhz_mwd_decode(N: int, phys) -> np.ndarray:
     """Minimum-weight decoding (exact, by enumeration; q_{N-1} = +1)."""
     out = np.zeros(N, np.int8)
     lib().orc_lhz_mwd_decode(N, np.ascontiguousarray(phys, np.int8), out)
+    return out
+
+
+def lhz_bp_decode(N: int, phys, error_rate: float, iterations: int, parent) -> np.ndarray:
+    """Belief-propagation decoding: iterated weighted majority over the N-2
+    parity checks of every pair, then a spanning-tree readout."""
+    out = np.zeros(N, np.int8)
+    lib().orc_lhz_bp_decode(N, np.ascontiguousarray(phys, np.int8), float(error_rate), int(iterations),
+                            np.ascontiguousarray(parent, np.int32), out)
     return out
 
 

@@ -19,6 +19,8 @@
  */
 #include <stdlib.h>
 
+#include <math.h>
+
 #include "oracle.h"
 
 void orc_me_decode(int32_t N, const int32_t *chain_sites, const int32_t *hub,
@@ -151,6 +153,45 @@ void orc_lhz_mwd_decode(int32_t N, const int8_t *phys, int8_t *logical)
             for (int32_t i = 0; i < N; i++) logical[i] = q[i];
         }
     }
+    free(q);
+}
+
+void orc_lhz_bp_decode(int32_t N, const int8_t *phys, double error_rate, int32_t iterations, const int32_t *parent,
+                       int8_t *logical)
+{
+    const double e = error_rate;
+    const double L0 = log((1.0 - e) / e);
+    const double L2 = log(((1.0 - e) * (1.0 - e) + e * e) / (2.0 * e * (1.0 - e)));
+    int8_t *p = (int8_t *)malloc((size_t)N * (size_t)N);
+    int8_t *q = (int8_t *)malloc((size_t)N * (size_t)N);
+    for (int32_t i = 0; i < N; i++)
+        for (int32_t j = 0; j < N; j++)
+            p[i * N + j] = i == j ? 1 : phys[orc_lhz_index(N, i < j ? i : j, i < j ? j : i)];
+    for (int32_t it = 0; it < iterations; it++) {
+        for (int32_t i = 0; i < N; i++)
+            for (int32_t j = 0; j < N; j++) {
+                if (i == j) {
+                    q[i * N + j] = 1;
+                    continue;
+                }
+                int32_t S = 0; /* the N-2 parity checks through a third logical spin */
+                for (int32_t l = 0; l < N; l++)
+                    if (l != i && l != j) S += p[i * N + l] * p[l * N + j];
+                const int32_t s = phys[orc_lhz_index(N, i < j ? i : j, i < j ? j : i)];
+                const double d = L0 * (double)s + L2 * (double)S;
+                q[i * N + j] = d > 0.0 ? 1 : (d < 0.0 ? -1 : p[i * N + j]);
+            }
+        int8_t *t = p;
+        p = q;
+        q = t;
+    }
+    /* spanning-tree readout of the pair values */
+    int8_t *pair = (int8_t *)malloc((size_t)N * (size_t)(N - 1) / 2 + 1);
+    for (int32_t i = 0; i < N; i++)
+        for (int32_t j = i + 1; j < N; j++) pair[orc_lhz_index(N, i, j)] = p[i * N + j];
+    orc_lhz_tree_decode(N, parent, pair, logical);
+    free(pair);
+    free(p);
     free(q);
 }
 

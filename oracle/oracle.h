@@ -159,6 +159,15 @@ void orc_lhz_tree_decode(int32_t N, const int32_t *parent, const int8_t *phys, i
  * i.e. the ground state of -sum_{i<j} s_ij q_i q_j.  q_{N-1} = +1; ties go to
  * the first state in binary order (bit i of x set <-> q_i = -1). */
 void orc_lhz_mwd_decode(int32_t N, const int8_t *phys, int8_t *logical);
+/* Belief-propagation decoding of an LHZ readout (Sec. IV, App. C): pair
+ * values p (starting from the readout s) updated `iterations` times, all
+ * pairs at once: p_ij <- sign(L0 s_ij + L2 sum_{l != i,j} p_il p_lj), ties
+ * keep p_ij, with L0 = ln((1-e)/e) the weight of a reading and
+ * L2 = ln(((1-e)^2 + e^2) / (2 e (1-e))) the weight of a two-reading parity
+ * check at error rate e; then the spanning tree `parent` reads out the
+ * logical state from p (q_0 = +1). */
+void orc_lhz_bp_decode(int32_t N, const int8_t *phys, double error_rate, int32_t iterations, const int32_t *parent,
+                       int8_t *logical);
 void orc_lhz_vote_decode(int32_t N, int32_t n_trees, const int32_t *parents,
                          const int8_t *phys, int8_t *logical);
 int64_t orc_logical_energy(int32_t N, const int32_t *J, const int8_t *s);

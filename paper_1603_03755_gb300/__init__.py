@@ -21,7 +21,7 @@ SQA_ERR_CUDA, SQA_ERR_TIMEOUT, SQA_ERR_NO_DEVICE, SQA_ERR_BUSY = -4, -5, -6, -7
 EMB = {"me": 0, "lhz": 1}
 KIND = {"sqa": 0, "pt": 1}
 MOVE = {"metropolis": 0, "wolff": 1}
-DECODE = {"me_mv": 0, "lhz_trees": 1, "lhz_star": 2, "lhz_chain": 3, "lhz_mwd": 4}
+DECODE = {"me_mv": 0, "lhz_trees": 1, "lhz_star": 2, "lhz_chain": 3, "lhz_mwd": 4, "lhz_bp": 5}
 
 LIB_PATH = _build.LIB
 
@@ -74,6 +74,8 @@ _SIGS = {
     "sqa_energies": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "sqa_decode": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_int32, C.c_void_p]),
+    "sqa_decode_bp": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_int32, C.c_void_p]),
     "sqa_ground_energy": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "sqa_ground_energy_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sqa_plan_terms": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
@@ -272,6 +274,18 @@ class Handle:
         p, dev = _ptr(out)
         _check(lib().sqa_energies(self._h, p, dev, _stream_ptr(stream)), "sqa_energies")
         return out
+
+    def decode_bp(self, error_rate: float = 0.2, iterations: int = 10, e_ground=None, stream=None):
+        """Belief-propagation decoding (LHZ); returns as decode()."""
+        logical = np.zeros((self.I, self.R, self.N), np.int8)
+        energy = np.zeros((self.I, self.R), np.int64)
+        succ = np.zeros(self.I, np.int32)
+        eg = None if e_ground is None else np.ascontiguousarray(e_ground, np.int64)
+        _check(lib().sqa_decode_bp(self._h, float(error_rate), int(iterations), logical.ctypes.data,
+                                   energy.ctypes.data, None if eg is None else eg.ctypes.data,
+                                   succ.ctypes.data if eg is not None else None, 0, _stream_ptr(stream)),
+               "sqa_decode_bp")
+        return logical, energy, (succ if eg is not None else None)
 
     def decode(self, method: str | None = None, n_trees: int = 0, e_ground=None, stream=None):
         """Host arrays: logical [I, R, N] int8, energy [I, R] int64, success [I] int32

@@ -854,15 +854,40 @@ sqa_status sqa_energies(sqa_handle *h, int32_t *out, int32_t out_is_device, void
     return SQA_OK;
 }
 
+static sqa_status decode_impl(sqa_handle *h, int32_t method, int32_t n_trees, double bp_error, int32_t bp_iters,
+                              int8_t *logical_out, int64_t *energy_out, const int64_t *e_ground,
+                              int32_t *success_out, int32_t out_is_device, void *stream);
+
 sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *logical_out,
                       int64_t *energy_out, const int64_t *e_ground, int32_t *success_out,
                       int32_t out_is_device, void *stream)
 {
+    return decode_impl(h, method, n_trees, 0.2, 10, logical_out, energy_out, e_ground, success_out, out_is_device,
+                       stream);
+}
+
+sqa_status sqa_decode_bp(sqa_handle *h, double error_rate, int32_t iterations, int8_t *logical_out,
+                         int64_t *energy_out, const int64_t *e_ground, int32_t *success_out,
+                         int32_t out_is_device, void *stream)
+{
+    if (!(error_rate > 0.0 && error_rate <= 0.5) || iterations < 0)
+        return set_error("error_rate in (0, 1/2], iterations >= 0"), SQA_ERR_INVALID;
+    return decode_impl(h, SQA_DECODE_LHZ_BP, 1, error_rate, iterations, logical_out, energy_out, e_ground,
+                       success_out, out_is_device, stream);
+}
+
+static sqa_status decode_impl(sqa_handle *h, int32_t method, int32_t n_trees, double bp_error, int32_t bp_iters,
+                              int8_t *logical_out, int64_t *energy_out, const int64_t *e_ground,
+                              int32_t *success_out, int32_t out_is_device, void *stream)
+{
     if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
     const bool me = h->emb == SQA_EMB_ME_CHIMERA;
     if (me != (method == SQA_DECODE_ME_MV) ||
-        (method < SQA_DECODE_ME_MV || method > SQA_DECODE_LHZ_MWD))
+        (method < SQA_DECODE_ME_MV || method > SQA_DECODE_LHZ_BP))
         return set_error("decode method does not match the embedding"), SQA_ERR_INVALID;
+    if (method == SQA_DECODE_LHZ_BP && h->N > 32)
+        return set_error("belief-propagation decoding keeps pair rows as 32-bit masks: N <= 32"),
+               SQA_ERR_UNSUPPORTED;
     if (method == SQA_DECODE_LHZ_MWD && h->N > 24)
         return set_error("minimum-weight decoding enumerates 2^(N-1) states: N <= 24"), SQA_ERR_UNSUPPORTED;
     if (method == SQA_DECODE_LHZ_TREES) {
@@ -876,7 +901,10 @@ sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *lo
     }
     cudaStream_t s = (cudaStream_t)stream;
     sqa_status st;
-    if (!me && method != SQA_DECODE_LHZ_MWD && (st = decode_trees(h, method, n_trees)) != SQA_OK) return st;
+    // belief propagation reads out with random tree 0
+    const int tree_method = method == SQA_DECODE_LHZ_BP ? SQA_DECODE_LHZ_TREES : method;
+    if (method == SQA_DECODE_LHZ_BP) n_trees = 1;
+    if (!me && method != SQA_DECODE_LHZ_MWD && (st = decode_trees(h, tree_method, n_trees)) != SQA_OK) return st;
     const size_t nrep = (size_t)h->I * h->R;
     DecodeArgs D{};
     D.method = method;
@@ -888,6 +916,19 @@ sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *lo
     D.parents = h->d_parents;
     D.orders = h->d_orders;
     D.J = h->d_J;
+    D.bp_iters = bp_iters;
+    if (method == SQA_DECODE_LHZ_BP) {
+        // decisions of sign(L0 s + L2 S) for s = +-1, S = -(N-2) .. N-2,
+        // evaluated in double on the host: 0 on an exact tie (keep the value)
+        const double e = bp_error;
+        const double L0 = log((1.0 - e) / e);
+        const double L2 = log(((1.0 - e) * (1.0 - e) + e * e) / (2.0 * e * (1.0 - e)));
+        for (int neg = 0; neg < 2; neg++)
+            for (int S = -(h->N - 2); S <= h->N - 2; S++) {
+                const double d = L0 * (double)(neg ? -1 : 1) + L2 * (double)S;
+                D.bp_dec[neg][S + h->N - 2] = (int8_t)(d > 0.0 ? 1 : (d < 0.0 ? -1 : 0));
+            }
+    }
     int8_t *d_log = logical_out;
     int64_t *d_en = energy_out, *d_eg = nullptr;
     int32_t *d_succ = success_out;

@@ -1062,6 +1062,40 @@ __global__ void decode_kernel(JobDev J, DecodeArgs D)
                 for (int k = 0; k < len; k++) sum += sig(D.chain[l * len + k]);
                 q[l] = (int8_t)(sum > 0 ? 1 : (sum < 0 ? -1 : sig(D.chain[l * len])));
             }
+        } else if (D.method == SQA_DECODE_LHZ_BP) {
+            // belief propagation: rows of pair values as bit masks (bit c of
+            // P[a] set <-> p_ac = -1); the N-2 checks of pair (a,c) sum to
+            // (N-2) - 2 popc((P[a] ^ P[c]) without bits a, c)
+            uint32_t P[32], S0[32], Q[32];
+            for (int a = 0; a < N; a++) {
+                uint32_t g = 0u;
+                for (int c = 0; c < N; c++)
+                    if (c != a && sig(D.pair[a * N + c]) < 0) g |= 1u << c;
+                P[a] = S0[a] = g;
+            }
+            const uint32_t all = N == 32 ? 0xFFFFFFFFu : ((1u << N) - 1u);
+            for (int it = 0; it < D.bp_iters; it++) {
+                for (int a = 0; a < N; a++) Q[a] = 0u;
+                for (int a = 0; a < N; a++)
+                    for (int c = a + 1; c < N; c++) {
+                        const int mis = __popc((P[a] ^ P[c]) & all & ~(1u << a) & ~(1u << c));
+                        const int S = (N - 2) - 2 * mis;
+                        const int dec = D.bp_dec[(S0[a] >> c) & 1u][S + N - 2];
+                        const bool neg = dec == 0 ? ((P[a] >> c) & 1u) != 0 : dec < 0;
+                        if (neg) {
+                            Q[a] |= 1u << c;
+                            Q[c] |= 1u << a;
+                        }
+                    }
+                for (int a = 0; a < N; a++) P[a] = Q[a];
+            }
+            const int *par = D.parents + (size_t)inst * D.n_trees * N;  // tree 0
+            const int *ord = D.orders + (size_t)inst * D.n_trees * N;
+            q[0] = 1;
+            for (int k = 1; k < N; k++) {
+                const int x = ord[k], p = par[x];
+                q[x] = (int8_t)(q[p] * (((P[p] >> x) & 1u) ? -1 : 1));
+            }
         } else if (D.method == SQA_DECODE_LHZ_MWD) {
             // minimum-weight decoding: walk the 2^(N-1) assignments with
             // q_{N-1} = +1 in Gray-code order; M counts the pair spins that

@@ -135,6 +135,8 @@ struct DecodeArgs {
     int8_t *logical;          // [I][R][N] or null
     int64_t *energy;          // [I][R] or null
     int32_t *success;         // [I] or null (zeroed by the host)
+    int bp_iters;             // belief propagation: iterations
+    int8_t bp_dec[2][64];     // [reading -1?][S + N - 2]: +1, -1, or 0 (keep)
 };
 
 // Builders (host_plan.cpp).

@@ -176,6 +176,8 @@ def _oracle_decode(pb, method, phys, seed, inst, n_trees):
         return O.lhz_tree_decode(N, O.chain_tree(N), phys)
     if method == "lhz_mwd":
         return O.lhz_mwd_decode(N, phys)
+    if method == "lhz_bp":
+        return O.lhz_bp_decode(N, phys, 0.2, 10, O.prufer_tree(N, seed, inst, 0))
     trees = np.stack([O.prufer_tree(N, seed, inst, t) for t in range(n_trees)])
     return O.lhz_vote_decode(N, trees, phys)
 
@@ -183,7 +185,7 @@ def _oracle_decode(pb, method, phys, seed, inst, n_trees):
 @pytest.mark.parametrize("emb,method,N", [("me", "me_mv", 8), ("me", "me_mv", 12),
                                           ("lhz", "lhz_trees", 8), ("lhz", "lhz_star", 6),
                                           ("lhz", "lhz_chain", 7), ("lhz", "lhz_mwd", 8),
-                                          ("lhz", "lhz_mwd", 11)])
+                                          ("lhz", "lhz_mwd", 11), ("lhz", "lhz_bp", 8), ("lhz", "lhz_bp", 13)])
 def test_decode_parity(emb, method, N):
     I, R, L, S = 3, 70, 8, 30
     pen = 6 if emb == "me" else 9
@@ -204,6 +206,23 @@ def test_decode_parity(emb, method, N):
             assert energy[i, r] == e
             cnt += e == eg[i]
         assert succ[i] == cnt
+
+
+@pytest.mark.parametrize("err,iters", [(0.2, 0), (0.1, 3), (0.35, 25), (0.5, 4)])
+def test_bp_decode_parameters(err, iters):
+    """sqa_decode_bp at other error rates and iteration counts (0 iterations:
+    the plain tree; 1/2: every decision ties) against the oracle."""
+    N, R = 9, 40
+    J = W.random_instances(N, 2, 71)
+    h = pkg.Handle(embedding="lhz", N=N, J=J, penalty=2, sweeps=15, R=R, seed=71, L=4, beta=1.0)
+    h.run(stream=0)
+    phys = pkg.unpack_words(h.readout(stream=0), R)
+    logical, _, _ = h.decode_bp(err, iters, stream=0)
+    for i in range(2):
+        tree = O.prufer_tree(N, 71, i, 0)
+        for r in range(R):
+            assert np.array_equal(logical[i, r], O.lhz_bp_decode(N, phys[i, :, r], err, iters, tree)), (i, r)
+    h.close()
 
 
 def test_mwd_decode_of_pt_readouts_k16():

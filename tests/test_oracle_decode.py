@@ -12,6 +12,8 @@
 import itertools
 from collections import Counter
 
+import math
+
 import numpy as np
 import pytest
 from scipy import stats
@@ -201,3 +203,81 @@ def test_mwd_corrects_flipped_pair_spins(N):
         flips = rng.choice(K, size=(N - 2) // 2, replace=False)
         bad[flips] *= -1
         assert np.array_equal(O.lhz_mwd_decode(N, bad), gauge)
+
+
+# ---------------------------------------------------------------------------
+# Belief-propagation decoding (Sec. IV, App. C; reading R21): iterated
+# weighted majority over the N-2 parity checks of every pair, then a tree.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N", [4, 7, 10])
+def test_bp_keeps_valid_states_and_corrects_one_flip(N):
+    """A valid state is a fixed point; one flipped pair spin is outvoted by
+    its N-2 agreeing checks (N >= 5 at error rate 0.2) and the tree reads the
+    encoded state."""
+    pb = O.Problem("lhz", N, W.random_couplings(N, 4), 3)
+    rng = np.random.default_rng(11 * N)
+    tree = O.prufer_tree(N, 9, 0, 0)
+    K = N * (N - 1) // 2
+    for _ in range(15):
+        s = np.where(rng.random(N) < 0.5, -1, 1).astype(np.int8)
+        gauge = s * s[0]
+        phys = pb.embed(s)
+        assert np.array_equal(O.lhz_bp_decode(N, phys, 0.2, 10, tree), gauge)
+        if N >= 5:
+            bad = phys.copy()
+            bad[rng.integers(K)] *= -1
+            assert np.array_equal(O.lhz_bp_decode(N, bad, 0.2, 10, tree), gauge)
+
+
+def test_bp_at_error_rate_one_half_is_the_plain_tree():
+    """At e = 1/2 a reading and a check carry no weight (L0 = L2 = 0): every
+    decision ties, the pair values stay the readout, and BP is the tree
+    decoder on the raw readout."""
+    N = 8
+    pb = O.Problem("lhz", N, W.random_couplings(N, 5), 3)
+    rng = np.random.default_rng(2)
+    tree = O.prufer_tree(N, 4, 1, 0)
+    for _ in range(20):
+        phys = _random_phys(pb, rng)
+        assert np.array_equal(O.lhz_bp_decode(N, phys, 0.5, 10, tree), O.lhz_tree_decode(N, tree, phys))
+
+
+@pytest.mark.parametrize("N", [6, 9])
+def test_bp_is_gauge_covariant(N):
+    """Flipping logical spin k of the encoding flips the N-1 pair spins at k;
+    BP must follow: the decoded state flips at k (k != 0, q_0 fixed) and
+    nowhere else, on corrupted readouts as well."""
+    pb = O.Problem("lhz", N, W.random_couplings(N, 6), 3)
+    rng = np.random.default_rng(5 * N)
+    tree = O.prufer_tree(N, 2, 0, 0)
+    for _ in range(20):
+        phys = _random_phys(pb, rng)
+        k = int(rng.integers(1, N))
+        flipped = phys.copy()
+        for l in range(N):
+            if l != k:
+                flipped[O.lhz_index(N, min(k, l), max(k, l))] *= -1
+        a = O.lhz_bp_decode(N, phys, 0.2, 10, tree)
+        b = O.lhz_bp_decode(N, flipped, 0.2, 10, tree)
+        want = a.copy()
+        want[k] *= -1
+        assert np.array_equal(b, want)
+
+
+def test_bp_worked_example_k4():
+    """K_4 readout with only pair (0,1) flipped, error rate 0.2, one
+    iteration.  Pair (0,1): reading -1 (weight L0 = ln 4 = 1.386), its two
+    checks through spins 2 and 3 both say +1 (weight L2 = ln(0.68/0.32) =
+    0.754 each): 2 x 0.754 > 1.386, so it turns +1.  Every other pair keeps
+    +1 (its checks cancel, its reading decides).  The star tree then reads
+    q = (+1, +1, +1, +1); with the checks counted through the pair itself
+    (three votes, one of them -1) the flip would survive."""
+    N = 4
+    phys = np.ones(6, np.int8)
+    phys[O.lhz_index(N, 0, 1)] = -1
+    star = O.star_tree(N)
+    assert O.lhz_bp_decode(N, phys, 0.2, 1, star).tolist() == [1, 1, 1, 1]
+    assert O.lhz_tree_decode(N, star, phys).tolist() == [1, -1, 1, 1]   # without BP
+    assert math.isclose(math.log(0.8 / 0.2), 1.3862943611198906)
+    assert 2 * math.log(0.68 / 0.32) > math.log(4.0) > math.log(0.68 / 0.32)

@@ -80,6 +80,14 @@ MUTANTS = [
     ("minimum-weight decoding maximises disagreement", "decode.c",
      "score += (int64_t)phys[orc_lhz_index(N, i, j)] * q[i] * q[j];",
      "score -= (int64_t)phys[orc_lhz_index(N, i, j)] * q[i] * q[j];"),
+    ("BP ties take +1", "decode.c", "q[i * N + j] = d > 0.0 ? 1 : (d < 0.0 ? -1 : p[i * N + j]);",
+     "q[i * N + j] = d >= 0.0 ? 1 : -1;"),
+    ("BP check weight without its factor 2", "decode.c",
+     "const double L2 = log(((1.0 - e) * (1.0 - e) + e * e) / (2.0 * e * (1.0 - e)));",
+     "const double L2 = log(((1.0 - e) * (1.0 - e) + e * e) / (e * (1.0 - e)));"),
+    ("BP checks through the pair itself", "decode.c",
+     "if (l != i && l != j) S += p[i * N + l] * p[l * N + j];",
+     "if (l != i) S += p[i * N + l] * p[l * N + j];"),
     ("ground-state enumeration half short", "decode.c",
      "int have = 0;\n    uint64_t count = (uint64_t)1 << (N - 1);\n    for (uint64_t x = 0; x < count; x++) {\n        for (int32_t i = 0; i < N - 1; i++) s[i]",
      "int have = 0;\n    uint64_t count = (uint64_t)1 << (N - 2);\n    for (uint64_t x = 0; x < count; x++) {\n        for (int32_t i = 0; i < N - 1; i++) s[i]"),
