@@ -872,11 +872,14 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 
 // One job: the descriptor is a kernel parameter, so its fields (the Philox
 // keys among them) are uniform across the grid.  One instantiation per path
-// (0 PT, 1 SQA windows, 2 SQA tables) so each gets its own registers.  Units
-// go to clusters in turn (all units of a job cost the same).
+// (0 PT, 1 SQA windows, 2 SQA tables, 3 / 4 SQA cluster moves) so each gets
+// its own registers: three blocks per SM (80 registers) for every path but
+// the cluster moves on rings of up to 64 slices, which fit four (64
+// registers, no spills).  Units go to clusters in turn (all units of a job
+// cost the same).
 template <int MODE>
-__global__ void __launch_bounds__(256, 3) sweep_kernel_one(const __grid_constant__ JobDev J, const Unit *units,
-                                                           int n_units, int *counter)
+__global__ void __launch_bounds__(256, MODE == 3 ? 4 : 3)
+    sweep_kernel_one(const __grid_constant__ JobDev J, const Unit *units, int n_units, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Smem sm = carve(J, smem_raw);

@@ -80,6 +80,13 @@ def test_sqa_edge_shapes(emb, N, L, R, S):
     sqa_case(emb, N, 2, L, R, S, 4, 1.3, seed=5)
 
 
+@pytest.mark.parametrize("emb,N,L,R,S", [("lhz", 64, 4, 32, 3),      # largest N: 2016 spins, 1891 plaquettes
+                                         ("me", 64, 4, 33, 3),      # largest N: 16 x 16 Chimera cells
+                                         ("lhz", 3, 1024, 40, 4)])  # largest L
+def test_sqa_maximum_sizes(emb, N, L, R, S):
+    sqa_case(emb, N, 2, L, R, S, 9 if emb == "lhz" else 6, 1.0, seed=64)
+
+
 def test_sqa_user_schedule_reaching_zero_field():
     S = 24
     A = np.linspace(1.0, 0.0, S)     # last sweep: A = 0, Jperp infinite
@@ -136,7 +143,8 @@ def test_batch_run_ragged_mix_equals_alone():
 
 
 @pytest.mark.parametrize("emb,N,P,R,S,swap", [("me", 5, 6, 40, 31, 3), ("lhz", 6, 8, 64, 20, 1),
-                                              ("me", 8, 1, 32, 12, 1), ("lhz", 4, 2, 100, 25, 2)])
+                                              ("me", 8, 1, 32, 12, 1), ("lhz", 4, 2, 100, 25, 2),
+                                              ("lhz", 64, 4, 32, 3, 1), ("me", 64, 3, 32, 3, 1)])
 def test_pt_parity(emb, N, P, R, S, swap):
     pen = 6 if emb == "me" else 9
     J = W.random_instances(N, 2, 21)
