@@ -86,3 +86,29 @@ def test_job_larger_than_budget_fails_cleanly():
     with pytest.raises(pkg.SQAError):
         srv.result(jid)
     srv.close()
+
+
+def test_a_failing_job_fails_alone():
+    """Jobs that cannot be planned (odd L; a cluster-move ring longer than
+    128 slices) fail with their own status while the jobs around them
+    finish with the same bits as alone; the worker keeps serving."""
+    good = _jobs()[:3]
+    bad_odd = dict(good[0], L=31)
+    bad_ring = dict(good[0], L=130, move="wolff")
+    srv = pkg.Server(mem_budget_bytes=1 << 32)
+    ids = [srv.submit(**kw) for kw in (good[0], bad_odd, good[1], bad_ring, good[2])]
+    for jid in ids:
+        srv.wait(jid, timeout=600)
+    states = [srv.poll(jid) for jid in ids]
+    assert [s["state"] for s in states] == ["done", "failed", "done", "failed", "done"]
+    assert states[1]["status"] == pkg.SQA_ERR_INVALID
+    assert states[3]["status"] == pkg.SQA_ERR_UNSUPPORTED
+    st = srv.stats()
+    assert st["jobs_done"] == 3 and st["jobs_failed"] == 2 and st["worker_status"] == 0
+    for jid, kw in zip([ids[0], ids[2], ids[4]], good):
+        got, _ = srv.result(jid)
+        h = pkg.Handle(**kw)
+        h.run(stream=0)
+        assert np.array_equal(got, h.state(stream=0))
+        h.close()
+    srv.close()
