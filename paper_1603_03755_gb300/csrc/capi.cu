@@ -62,8 +62,9 @@ sqa_status device_ready()
         SQA_CUDA(cudaGetDeviceProperties(&prop, dev));
         cudaFuncAttributes fa;
         SQA_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel));
-        const void *ks[6] = {(const void *)sweep_kernel,   sweep_one_entry_mode(0), sweep_one_entry_mode(1),
-                             sweep_one_entry_mode(2), sweep_one_entry_mode(3), sweep_one_entry_mode(4)};
+        const void *ks[7] = {(const void *)sweep_kernel,   sweep_one_entry_mode(0), sweep_one_entry_mode(1),
+                             sweep_one_entry_mode(2), sweep_one_entry_mode(3), sweep_one_entry_mode(4),
+                             sweep_one_entry_mode(5)};
         int limit = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
         for (const void *k : ks) {
             cudaFuncAttributes fk;
@@ -73,7 +74,7 @@ sqa_status device_ready()
         for (const void *k : ks) SQA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
         // single-job kernels may run 16-block clusters (one unit over 16 SMs'
         // worth of blocks); where the device refuses, clusters stop at 8
-        for (int m = 0; m < 5; m++)
+        for (int m = 0; m < 6; m++)
             if (cudaFuncSetAttribute(sweep_one_entry_mode(m), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                 cudaSuccess)
                 cudaGetLastError();
@@ -320,6 +321,8 @@ sqa_status setup_program(sqa_handle *h)
     J.key_lo = shi ^ kDomSweepLo;
     J.key_swap = shi ^ kDomSwap;
     J.move = wolff ? SQA_MOVE_WOLFF : SQA_MOVE_METROPOLIS;
+    J.pairs = 1;
+    for (const PlanTerm &t : pl.terms) J.pairs = J.pairs && t.size == 2;
     J.key_wstart = shi ^ kDomWStart;
     J.key_wbond = shi ^ kDomWBond;
     J.key_wacc = shi ^ kDomWAcc;

@@ -130,6 +130,8 @@ __device__ __forceinline__ uint32_t sub_carry_into(uint32_t x, uint32_t q, uint3
 
 // Term planes of one item: bit b of pl[k] is set when term k's value is
 // negative for replica b (it turns positive on a flip).  kw[k] is K*|w_k|.
+// PAIRS: every term has exactly one other member (minor embedding).
+template <bool PAIRS>
 __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *row, int wc, int w,
                                             uint32_t s, uint32_t (&pl)[kMaxTerms],
                                             uint32_t (&kw)[kMaxTerms])
@@ -141,9 +143,13 @@ __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *r
         if (k < sr.nterm) {
             const TermRec tr = sr.t[k];
             uint32_t p = s;
-            if (tr.p[0] >= 0) p ^= row[tr.p[0] * wc + w];
-            if (tr.p[1] >= 0) p ^= row[tr.p[1] * wc + w];
-            if (tr.p[2] >= 0) p ^= row[tr.p[2] * wc + w];
+            if (PAIRS) {
+                p ^= row[tr.p[0] * wc + w];
+            } else {
+                if (tr.p[0] >= 0) p ^= row[tr.p[0] * wc + w];
+                if (tr.p[1] >= 0) p ^= row[tr.p[1] * wc + w];
+                if (tr.p[2] >= 0) p ^= row[tr.p[2] * wc + w];
+            }
             const int wv = tr.w;
             // w * prod(sigma) is negative iff (product is -1) xor (w < 0)
             pl[k] = p ^ (uint32_t)(wv >> 31);
@@ -236,7 +242,7 @@ __device__ __forceinline__ int full_index(const SiteRec &sr, uint32_t code)
 // One item: the word of 32 replicas of site si at local slice/slot zl.  Byte r
 // of code[j] selects replica j + 8r's threshold: a per-site table entry (SQA,
 // table mode) or an index in the site's window of the threshold row.
-template <int KIND, bool LUT>
+template <int KIND, bool LUT, bool PAIRS = false>
 __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const Smem &sm, const Part &pt,
                                            int inst, int w0, int wc, int t, int si, int zl, int w)
 {
@@ -248,7 +254,7 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
     uint32_t code[8];
     {
         uint32_t pl[kMaxTerms], kw[kMaxTerms];
-        term_planes(sr, row, wc, w, s, pl, kw);
+        term_planes<PAIRS>(sr, row, wc, w, s, pl, kw);
         uint32_t d1 = 0u, d2 = 0u;
         if (KIND == SQA_KIND_SQA) {
             // temporal disagreements: m = sigma (sigma_up + sigma_dn) = 2 - 2 (d1 + d2)
@@ -785,7 +791,7 @@ __device__ void run_unit_wolff(const JobDev &J, const Smem &sm, const Unit &u)
     __syncthreads();
 }
 
-template <int KIND, bool LUT>
+template <int KIND, bool LUT, bool PAIRS = false>
 __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 {
     const int nthr = blockDim.x, tid = threadIdx.x;
@@ -845,7 +851,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 for (int it = tid; it < nitems; it += nthr) {
                     const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
                     const int q = (int)fdiv((uint32_t)r, div_z), zh = r - q * half;
-                    sweep_item<SQA_KIND_SQA, LUT>(J, K, sm, pt, inst, w0, wc, t, c0 + q, 2 * zh + par, w);
+                    sweep_item<SQA_KIND_SQA, LUT, PAIRS>(J, K, sm, pt, inst, w0, wc, t, c0 + q, 2 * zh + par, w);
                 }
                 cluster_barrier(pt.C);  // neighbouring blocks read this phase's boundary slices
             }
@@ -872,7 +878,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 
 // One job: the descriptor is a kernel parameter, so its fields (the Philox
 // keys among them) are uniform across the grid.  One instantiation per path
-// (0 PT, 1 SQA windows, 2 SQA tables, 3 / 4 SQA cluster moves) so each gets
+// (0 PT, 1 SQA windows, 2 / 5 SQA tables, 3 / 4 SQA cluster moves) so each gets
 // its own registers: three blocks per SM (80 registers) for every path but
 // the cluster moves on rings of up to 64 slices, which fit four (64
 // registers, no spills).  Units go to clusters in turn (all units of a job
@@ -891,6 +897,8 @@ __global__ void __launch_bounds__(256, MODE == 3 ? 4 : 3)
             run_unit<SQA_KIND_PT, false>(J, sm, u);
         else if (MODE == 2)
             run_unit<SQA_KIND_SQA, true>(J, sm, u);
+        else if (MODE == 5)
+            run_unit<SQA_KIND_SQA, true, true>(J, sm, u);
         else if (MODE == 3)
             run_unit_wolff<2>(J, sm, u);
         else if (MODE == 4)
@@ -903,12 +911,13 @@ __global__ void __launch_bounds__(256, MODE == 3 ? 4 : 3)
 // Host side of the single-job kernel: its entry for a job's path, and the
 // launch (a cluster launch when the job's units span several blocks).
 // Modes: 0 PT, 1 SQA windows, 2 SQA tables, 3 / 4 SQA cluster moves with
-// 2 / 4 slices per lane (L <= 64 / L <= 128).
+// 2 / 4 slices per lane (L <= 64 / L <= 128), 5 SQA tables with two-spin
+// terms only (minor embedding).
 static int one_mode(const JobDev &J)
 {
     if (J.kind == SQA_KIND_PT) return 0;
     if (J.move == SQA_MOVE_WOLFF) return J.Z <= 64 ? 3 : 4;
-    return J.use_lut ? 2 : 1;
+    return J.use_lut ? (J.pairs ? 5 : 2) : 1;
 }
 
 const void *sweep_one_entry_mode(int mode)
@@ -918,7 +927,8 @@ const void *sweep_one_entry_mode(int mode)
     case 1: return (const void *)sweep_kernel_one<1>;
     case 2: return (const void *)sweep_kernel_one<2>;
     case 3: return (const void *)sweep_kernel_one<3>;
-    default: return (const void *)sweep_kernel_one<4>;
+    case 4: return (const void *)sweep_kernel_one<4>;
+    default: return (const void *)sweep_kernel_one<5>;
     }
 }
 
@@ -944,7 +954,8 @@ cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, in
     case 1: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<1>, J, units, n_units, counter);
     case 2: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<2>, J, units, n_units, counter);
     case 3: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<3>, J, units, n_units, counter);
-    default: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<4>, J, units, n_units, counter);
+    case 4: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<4>, J, units, n_units, counter);
+    default: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<5>, J, units, n_units, counter);
     }
 }
 

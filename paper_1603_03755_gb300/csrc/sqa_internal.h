@@ -88,6 +88,7 @@ struct JobDev {
     int n_ecls;      // weight classes used (max over instances); 0 = too many distinct weights
     int csize;       // blocks per unit (a thread-block cluster when > 1)
     int zr;          // slices (SQA) or slots (PT) per block: Z / csize
+    int pairs;       // every term has two spins (minor embedding)
     // time-like cluster moves (SQA, move == SQA_MOVE_WOLFF)
     int move;
     uint32_t key_wstart, key_wbond, key_wacc;  // seed_hi ^ kDomW*
