@@ -62,9 +62,9 @@ sqa_status device_ready()
         SQA_CUDA(cudaGetDeviceProperties(&prop, dev));
         cudaFuncAttributes fa;
         SQA_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel));
-        const void *ks[7] = {(const void *)sweep_kernel,   sweep_one_entry_mode(0), sweep_one_entry_mode(1),
+        const void *ks[8] = {(const void *)sweep_kernel,   sweep_one_entry_mode(0), sweep_one_entry_mode(1),
                              sweep_one_entry_mode(2), sweep_one_entry_mode(3), sweep_one_entry_mode(4),
-                             sweep_one_entry_mode(5)};
+                             sweep_one_entry_mode(5), sweep_one_entry_mode(6)};
         int limit = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
         for (const void *k : ks) {
             cudaFuncAttributes fk;
@@ -74,7 +74,7 @@ sqa_status device_ready()
         for (const void *k : ks) SQA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
         // single-job kernels may run 16-block clusters (one unit over 16 SMs'
         // worth of blocks); where the device refuses, clusters stop at 8
-        for (int m = 0; m < 6; m++)
+        for (int m = 0; m < 7; m++)
             if (cudaFuncSetAttribute(sweep_one_entry_mode(m), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                 cudaSuccess)
                 cudaGetLastError();

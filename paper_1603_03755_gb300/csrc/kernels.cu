@@ -862,7 +862,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 for (int it = tid; it < nitems; it += nthr) {
                     const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
                     const int q = (int)fdiv((uint32_t)r, div_z), p = r - q * zr;
-                    sweep_item<SQA_KIND_PT, false>(J, K, sm, pt, inst, w0, wc, t, c0 + q, p, w);
+                    sweep_item<SQA_KIND_PT, false, PAIRS>(J, K, sm, pt, inst, w0, wc, t, c0 + q, p, w);
                 }
                 __syncthreads();
             }
@@ -878,7 +878,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 
 // One job: the descriptor is a kernel parameter, so its fields (the Philox
 // keys among them) are uniform across the grid.  One instantiation per path
-// (0 PT, 1 SQA windows, 2 / 5 SQA tables, 3 / 4 SQA cluster moves) so each gets
+// (0 / 6 PT, 1 SQA windows, 2 / 5 SQA tables, 3 / 4 SQA cluster moves) so each gets
 // its own registers: three blocks per SM (80 registers) for every path but
 // the cluster moves on rings of up to 64 slices, which fit four (64
 // registers, no spills).  Units go to clusters in turn (all units of a job
@@ -895,6 +895,8 @@ __global__ void __launch_bounds__(256, MODE == 3 ? 4 : 3)
         const Unit u = units[ui];
         if (MODE == 0)
             run_unit<SQA_KIND_PT, false>(J, sm, u);
+        else if (MODE == 6)
+            run_unit<SQA_KIND_PT, false, true>(J, sm, u);
         else if (MODE == 2)
             run_unit<SQA_KIND_SQA, true>(J, sm, u);
         else if (MODE == 5)
@@ -911,11 +913,11 @@ __global__ void __launch_bounds__(256, MODE == 3 ? 4 : 3)
 // Host side of the single-job kernel: its entry for a job's path, and the
 // launch (a cluster launch when the job's units span several blocks).
 // Modes: 0 PT, 1 SQA windows, 2 SQA tables, 3 / 4 SQA cluster moves with
-// 2 / 4 slices per lane (L <= 64 / L <= 128), 5 SQA tables with two-spin
-// terms only (minor embedding).
+// 2 / 4 slices per lane (L <= 64 / L <= 128), 5 / 6 SQA tables / PT with
+// two-spin terms only (minor embedding).
 static int one_mode(const JobDev &J)
 {
-    if (J.kind == SQA_KIND_PT) return 0;
+    if (J.kind == SQA_KIND_PT) return J.pairs ? 6 : 0;
     if (J.move == SQA_MOVE_WOLFF) return J.Z <= 64 ? 3 : 4;
     return J.use_lut ? (J.pairs ? 5 : 2) : 1;
 }
@@ -928,7 +930,8 @@ const void *sweep_one_entry_mode(int mode)
     case 2: return (const void *)sweep_kernel_one<2>;
     case 3: return (const void *)sweep_kernel_one<3>;
     case 4: return (const void *)sweep_kernel_one<4>;
-    default: return (const void *)sweep_kernel_one<5>;
+    case 5: return (const void *)sweep_kernel_one<5>;
+    default: return (const void *)sweep_kernel_one<6>;
     }
 }
 
@@ -955,7 +958,8 @@ cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, in
     case 2: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<2>, J, units, n_units, counter);
     case 3: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<3>, J, units, n_units, counter);
     case 4: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<4>, J, units, n_units, counter);
-    default: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<5>, J, units, n_units, counter);
+    case 5: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<5>, J, units, n_units, counter);
+    default: return cudaLaunchKernelEx(&cfg, sweep_kernel_one<6>, J, units, n_units, counter);
     }
 }
 
