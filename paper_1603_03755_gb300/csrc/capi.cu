@@ -133,7 +133,8 @@ void free_all(sqa_handle *h, cudaStream_t s = 0)
 // slot for PT); pad the row so those lanes fall on distinct banks.
 int zstride_for(const JobDev &J, int wc)
 {
-    int zs = J.n * wc;
+    // the n used sites and a zero slot (site n) that absent term members read
+    int zs = (J.n + 1) * wc;
     if (J.kind == SQA_KIND_SQA && J.move == SQA_MOVE_WOLFF) {
         // cluster moves: a warp reads 32 consecutive rows, on distinct banks
         // when the row stride is odd

@@ -130,9 +130,10 @@ __device__ __forceinline__ uint32_t sub_carry_into(uint32_t x, uint32_t q, uint3
 
 // Term planes of one item: bit b of pl[k] is set when term k's value is
 // negative for replica b (it turns positive on a flip).  kw[k] is K*|w_k|.
-// PAIRS: every term has exactly one other member (minor embedding).
+// PAIRS: every term has exactly one other member (minor embedding);
+// otherwise absent members read the zero word of site n (branch-free).
 template <bool PAIRS>
-__device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *row, int wc, int w,
+__device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *row, int n, int wc, int w,
                                             uint32_t s, uint32_t (&pl)[kMaxTerms],
                                             uint32_t (&kw)[kMaxTerms])
 {
@@ -146,9 +147,11 @@ __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *r
             if (PAIRS) {
                 p ^= row[tr.p[0] * wc + w];
             } else {
-                if (tr.p[0] >= 0) p ^= row[tr.p[0] * wc + w];
-                if (tr.p[1] >= 0) p ^= row[tr.p[1] * wc + w];
-                if (tr.p[2] >= 0) p ^= row[tr.p[2] * wc + w];
+                // an absent member (-1) reads the row's zero slot at site n
+                const uint32_t z = (uint32_t)n;
+                p ^= row[min((uint32_t)(int)tr.p[0], z) * wc + w];
+                p ^= row[min((uint32_t)(int)tr.p[1], z) * wc + w];
+                p ^= row[min((uint32_t)(int)tr.p[2], z) * wc + w];
             }
             const int wv = tr.w;
             // w * prod(sigma) is negative iff (product is -1) xor (w < 0)
@@ -254,7 +257,7 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
     uint32_t code[8];
     {
         uint32_t pl[kMaxTerms], kw[kMaxTerms];
-        term_planes<PAIRS>(sr, row, wc, w, s, pl, kw);
+        term_planes<PAIRS>(sr, row, J.n, wc, w, s, pl, kw);
         uint32_t d1 = 0u, d2 = 0u;
         if (KIND == SQA_KIND_SQA) {
             // temporal disagreements: m = sigma (sigma_up + sigma_dn) = 2 - 2 (d1 + d2)
@@ -766,6 +769,7 @@ __device__ void run_unit_wolff(const JobDev &J, const Smem &sm, const Unit &u)
         const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
         sm.S[(size_t)zl * J.zstride + si * wc + w] = J.state[(((size_t)inst * Z + zl) * n + si) * J.W + w0 + w];
     }
+    for (int i = tid; i < Z * wc; i += nthr) sm.S[(size_t)(i / wc) * J.zstride + n * wc + i % wc] = 0u;
     {
         const uint32_t *src = (const uint32_t *)(J.sites + (size_t)inst * n);
         uint32_t *dst = (uint32_t *)sm.sites;
@@ -810,12 +814,13 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
     }
     pt.z0 = pt.rank * pt.zr;
     const int zr = pt.zr, z0 = pt.z0;
-    // stage this block's slices and the site records
+    // stage this block's slices (and each row's zero slot) and the site records
     for (int i = tid; i < zr * n * wc; i += nthr) {
         const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
         sm.S[(size_t)zl * J.zstride + si * wc + w] =
             J.state[(((size_t)inst * Z + z0 + zl) * n + si) * J.W + w0 + w];
     }
+    for (int i = tid; i < zr * wc; i += nthr) sm.S[(size_t)(i / wc) * J.zstride + n * wc + i % wc] = 0u;
     {
         const uint32_t *src = (const uint32_t *)(J.sites + (size_t)inst * n);
         uint32_t *dst = (uint32_t *)sm.sites;

@@ -14,7 +14,7 @@
 namespace sqa {
 
 struct SmemOffsets {
-    size_t S;      // state [zr][zstride] words (this block's slices or slots)
+    size_t S;      // state [zr][zstride] words (this block's slices or slots; word n*wc.. of a row: zero slot)
     size_t T;      // full thresholds: SQA one row, PT P rows
     size_t Tq;     // high halves of the thresholds (T & 0xFFFF0000): PT P rows, SQA window mode one row
     size_t lut;    // SQA: per-site tables of threshold high halves
