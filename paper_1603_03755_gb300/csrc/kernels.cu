@@ -1008,12 +1008,16 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const
         if (s_job.csize != 1) continue;  // units of this kernel live in one block
         const Unit u = units[ui];
         const Smem sm = carve(s_job, smem_raw);
-        if (s_job.kind == SQA_KIND_PT)
+        if (s_job.kind == SQA_KIND_PT && s_job.pairs)
+            run_unit<SQA_KIND_PT, false, true>(s_job, sm, u);
+        else if (s_job.kind == SQA_KIND_PT)
             run_unit<SQA_KIND_PT, false>(s_job, sm, u);
         else if (s_job.move == SQA_MOVE_WOLFF && s_job.Z <= 64)
             run_unit_wolff<2>(s_job, sm, u);
         else if (s_job.move == SQA_MOVE_WOLFF)
             run_unit_wolff<4>(s_job, sm, u);
+        else if (s_job.use_lut && s_job.pairs)
+            run_unit<SQA_KIND_SQA, true, true>(s_job, sm, u);
         else if (s_job.use_lut)
             run_unit<SQA_KIND_SQA, true>(s_job, sm, u);
         else
