@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--per-instance-sample", type=int, default=8,
                     help="instances timed on the one-launch-per-instance path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the planner's launch shape (profiling captures then see only timed launches)")
     ap.add_argument("--no-extra", action="store_true", help="skip the ragged-batch and PT workloads")
     ap.add_argument("--pt-sweeps", type=int, default=100_000)
     ap.add_argument("--ragged-sweeps", type=int, default=10_000)
@@ -462,7 +464,8 @@ def main():
     h = pkg.Handle(embedding="me", N=N, J=cfg["J"], penalty=cfg["penalty"], sweeps=S, R=R,
                    seed=cfg["seed"], L=L, beta=cfg["beta"])
     attempts = h.info["attempts_per_sweep"] * S
-    tuned = h.autotune(n_trial=20, stream=sp)            # launch shape by measurement
+    tuned = (h.autotune(n_trial=20, stream=sp) if not args.no_autotune  # launch shape by measurement
+             else {"trial_attempts_per_s": None})
     e_ground = pkg.ground_energy(N, cfg["J"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     E_dev = torch.empty((I, L, R), dtype=torch.int32, device=dev)
