@@ -728,10 +728,10 @@ __device__ __forceinline__ void wolff_item(const JobDev &J, const Smem &sm, uint
                 uint32_t v = 0u;
                 if (tau < L) {
                     const uint32_t *row = sm.S + (size_t)tau * J.zstride;
-                    v = s[j];
-                    if (tr.p[0] >= 0) v ^= row[tr.p[0] * wc + w];
-                    if (tr.p[1] >= 0) v ^= row[tr.p[1] * wc + w];
-                    if (tr.p[2] >= 0) v ^= row[tr.p[2] * wc + w];
+                    // absent members (-1) read the row's zero slot at site n
+                    const uint32_t zs = (uint32_t)J.n;
+                    v = s[j] ^ row[min((uint32_t)(int)tr.p[0], zs) * wc + w] ^
+                        row[min((uint32_t)(int)tr.p[1], zs) * wc + w] ^ row[min((uint32_t)(int)tr.p[2], zs) * wc + w];
                     v = (v ^ (uint32_t)((int)tr.w >> 31)) & C[j];  // term negative, slice in the cluster
                 }
                 cnt += __popc(warp_transpose(v, lane));
