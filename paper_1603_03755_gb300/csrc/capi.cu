@@ -20,6 +20,8 @@ __global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units,
 // The single-job sweep kernel (kernels.cu), one instantiation per path.
 const void *sweep_one_entry(const JobDev &J);
 const void *sweep_one_entry_mode(int mode);
+// Threads per block of the single-job kernel on a job's path.
+int sweep_one_threads(const JobDev &J);
 cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, int *counter, int grid,
                              cudaStream_t s);
 int max_active_clusters(const JobDev &J);
@@ -158,10 +160,10 @@ int unit_smem(const JobDev &J, int wc, int *zstride_out)
     return (int)smem_layout(J, wc, zs).total;
 }
 
-int blocks_per_sm(const void *kernel, int smem)
+int blocks_per_sm(const void *kernel, int smem, int threads = kThreads)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -203,7 +205,7 @@ sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> 
                         J.smem_bytes = smem;
                         J.wc = wc;
                         J.zstride = zs;
-                        const int active = C == 1 ? blocks_per_sm(one_kernel(J), smem) * g_num_sms
+                        const int active = C == 1 ? blocks_per_sm(one_kernel(J), smem, sweep_one_threads(J)) * g_num_sms
                                                   : max_active_clusters(J);
                         const int64_t n_units = (int64_t)h->I * ((J.W + wc - 1) / wc);
                         // PT clusters exchange boundary slots every swap event:
@@ -412,7 +414,7 @@ sqa_status launch_sweeps(sqa_handle *h, int t0, int t1, int u0, int nu, cudaStre
     SQA_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
     int grid;
     if (h->job.csize == 1)
-        grid = grid_for(one_kernel(h->job), h->job.smem_bytes, nu);
+        grid = grid_for(one_kernel(h->job), h->job.smem_bytes, nu, sweep_one_threads(h->job));
     else
         grid = std::max(1, std::min(nu, max_active_clusters(h->job))) * h->job.csize;
     SQA_CUDA(launch_sweep_one(h->job, h->d_units + u0, nu, h->d_counter, grid, s));
@@ -456,9 +458,9 @@ sqa_status launch_init(sqa_handle *h, cudaStream_t s)
     return SQA_OK;
 }
 
-int grid_for(const void *kernel, int smem_bytes, int n_units)
+int grid_for(const void *kernel, int smem_bytes, int n_units, int threads)
 {
-    int per_sm = std::max(blocks_per_sm(kernel, smem_bytes), 1);
+    int per_sm = std::max(blocks_per_sm(kernel, smem_bytes, threads), 1);
     return std::max(1, std::min(n_units, per_sm * g_num_sms));
 }
 
@@ -525,7 +527,7 @@ cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, i
 {
     int grid;
     if (J.csize == 1)
-        grid = grid_for(sweep_one_entry(J), J.smem_bytes, n_units);
+        grid = grid_for(sweep_one_entry(J), J.smem_bytes, n_units, sweep_one_threads(J));
     else
         grid = std::max(1, std::min(n_units, max_active_clusters(J))) * J.csize;
     return launch_sweep_one(J, units, n_units, counter, grid, s);

@@ -57,7 +57,7 @@ sqa_status cuda_fail(cudaError_t e, const char *where);
 // Draws fresh initial spins for every instance of h on stream s.
 sqa_status launch_init(sqa_handle *h, cudaStream_t s);
 // Blocks for one launch of kernel over n_units units (at most one wave).
-int grid_for(const void *kernel, int smem_bytes, int n_units);
+int grid_for(const void *kernel, int smem_bytes, int n_units, int threads = kThreads);
 // The multi-job sweep kernel (kernels.cu).
 __global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units, int *counter);
 // Device bytes sqa_create would allocate for desc (host-only estimate, exact

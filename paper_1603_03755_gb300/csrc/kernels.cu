@@ -884,12 +884,14 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 // One job: the descriptor is a kernel parameter, so its fields (the Philox
 // keys among them) are uniform across the grid.  One instantiation per path
 // (0 / 6 PT, 1 SQA windows, 2 / 5 SQA tables, 3 / 4 SQA cluster moves) so each gets
-// its own registers: three blocks per SM (80 registers) for every path but
-// the cluster moves on rings of up to 64 slices, which fit four (64
-// registers, no spills).  Units go to clusters in turn (all units of a job
+// its own registers: three blocks of 256 threads per SM (80 registers) for
+// the SQA paths but the cluster moves on rings of up to 64 slices, which fit
+// four (64 registers, no spills); PT runs two blocks of 384 threads (a PT
+// job usually has one unit per ladder, fewer units than block slots, so
+// wider blocks give the busy SMs more warps).  Units go to clusters in turn (all units of a job
 // cost the same).
 template <int MODE>
-__global__ void __launch_bounds__(256, MODE == 3 ? 4 : 3)
+__global__ void __launch_bounds__(MODE == 0 || MODE == 6 ? 384 : 256, MODE == 3 ? 4 : (MODE == 0 || MODE == 6 ? 2 : 3))
     sweep_kernel_one(const __grid_constant__ JobDev J, const Unit *units, int n_units, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -942,12 +944,18 @@ const void *sweep_one_entry_mode(int mode)
 
 const void *sweep_one_entry(const JobDev &J) { return sweep_one_entry_mode(one_mode(J)); }
 
+int sweep_one_threads(const JobDev &J)
+{
+    const int m = one_mode(J);
+    return m == 0 || m == 6 ? 384 : 256;
+}
+
 cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, int *counter, int grid,
                              cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3((unsigned)sweep_one_threads(J));
     cfg.dynamicSmemBytes = (size_t)J.smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -973,7 +981,7 @@ int max_active_clusters(const JobDev &J)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)J.csize * 1024u);
-    cfg.blockDim = dim3(256);
+    cfg.blockDim = dim3((unsigned)sweep_one_threads(J));
     cfg.dynamicSmemBytes = (size_t)J.smem_bytes;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
