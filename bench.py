@@ -73,18 +73,27 @@ def parse():
     return ap.parse_args()
 
 
+def kernels_code_sha256(path):
+    """SHA-256 of a CUDA source with its comments and whitespace removed, so
+    that the record below follows the code, not the comments."""
+    import hashlib
+    import re
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()
+
+
 def kernel_traffic(n_instances):
     """DRAM bytes of one sweep launch from the committed ncu capture of the
     sweep kernel (read + write, per instance, scaled to n_instances), or None
-    when kernels.cu changed since that capture."""
-    import hashlib
+    when the code of kernels.cu changed since that capture."""
     p = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
     src = os.path.join(ROOT, "paper_1603_03755_gb300", "csrc", "kernels.cu")
     if not os.path.exists(p):
         return None, "no capture"
     rec = json.load(open(p))
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if rec.get("kernels_cu_sha256") != sha:
+    if rec.get("kernels_cu_code_sha256") != kernels_code_sha256(src):
         return None, "kernel changed since the capture"
     return rec["dram_bytes_per_instance"] * n_instances, rec["note"]
 

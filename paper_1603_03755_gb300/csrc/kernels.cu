@@ -6,21 +6,26 @@
 // graph colour), z the Trotter slice (SQA) or temperature slot (PT).
 //
 // Work.  A unit is a run of words of one instance; replicas in different
-// words never interact, so a unit is an independent system.  The persistent
-// sweep kernel pulls units from a global counter, stages the unit's state,
-// its site records and its threshold rows in shared memory, runs every sweep
-// of the launch there and writes the state back.  Within a sweep the colour
-// classes (SQA: colour x slice parity; PT: colour) run in order with a block
+// words never interact, so a unit is an independent system.  The single-job
+// sweep kernel gives units to blocks (or thread-block clusters, which split a
+// unit's slices or slots) in turn; the multi-job kernel of ragged batches
+// and the serving loop pulls them from a counter.  A block stages its
+// unit's state, site records and threshold rows in shared memory, runs every
+// sweep of the launch there and writes the state back.  Within a sweep the
+// colour classes (SQA: colour x slice parity; PT: colour) run in order with a
 // barrier between them; all items of a class are independent.
 //
-// Per item (site, z, word) the kernel forms, for each term of the site, the
-// word of replicas whose term value is negative (XOR of the members' words,
-// inverted for negative weights).  Four replicas at a time (bits j, j+8,
-// j+16, j+24) it then sums the weighted term bits and the temporal
-// disagreements byte-wise into the site's window of the threshold row,
-// loads the four thresholds and compares them with the high 16 bits of the
-// replicas' uniforms; only when those bits tie with the threshold's high
-// half is the low half drawn (probability 2^-16).
+// Per item (site, z, word) the single-spin sweep draws the item's four
+// Philox blocks (16 high uniform bits per replica), forms for each term of
+// the site the word of replicas whose term value is negative (and, for SQA,
+// the two temporal disagreement words), turns them into one threshold index
+// per replica (a per-site code table after an 8x8 bit-matrix transpose, or
+// byte-wise sums into the site's window of the threshold row), and compares
+// the uniforms' high halves with the thresholds' through the carry of a
+// subtraction; only a tie of the high halves draws the low half
+// (probability 2^-16).  PT recounts energies for its swaps in bit-sliced
+// form.  The time-like cluster moves work one warp per (site, word) on the
+// site's whole imaginary-time ring.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
