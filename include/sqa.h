@@ -14,9 +14,13 @@
  *   over the L Trotter slices of the path-integral representation of
  *   H(t) = A(t) H_X + B(t) H_P (Eq. 3, App. B); PT runs the same sweep at zero
  *   transverse field on P temperature slots with neighbour swaps accepted with
- *   probability min{1, exp[(E_{i+1}-E_i)(beta_{i+1}-beta_i)]} (Eq. 9).
- *   Readouts are decoded by majority vote (Eqs. 4-5) or LHZ spanning trees
- *   (App. A, Eqs. 10-11).
+ *   probability min{1, exp[(E_{i+1}-E_i)(beta_{i+1}-beta_i)]} (Eq. 9).  SQA
+ *   can also run time-like cluster (Wolff) moves, the paper's own SQA update
+ *   (Sec. III).  Readouts are decoded by majority vote (Eqs. 4-5), LHZ
+ *   spanning trees (App. A, Eqs. 10-11), LHZ minimum-weight decoding
+ *   (Sec. IV A) or LHZ belief propagation (Sec. IV, App. C).  Batches of
+ *   jobs run in one persistent launch (replayable from a CUDA graph), and a
+ *   server serves a stream of jobs with continuous batching.
  *
  * Conventions
  *   - Every call returns an sqa_status and never aborts the process.
