@@ -158,7 +158,11 @@ sqa_status sqa_run_per_instance(sqa_handle *h, void *stream);
 
 /* Parallel tempering on the handle's problem (App. B): switches the handle to
  * PT with the given ladder (betas strictly decreasing, coldest first), draws
- * fresh spins and runs n_sweeps sweeps with swaps every swap_every sweeps. */
+ * fresh spins and runs n_sweeps sweeps with swaps every swap_every sweeps.
+ * Synchronises stream, then replaces the handle's device program; when the
+ * new one cannot be set up (SQA_ERR_UNSUPPORTED: couplings and penalty too
+ * large for PT's byte-wise windows; SQA_ERR_NOMEM) the handle is left with
+ * none, and every later call on it but sqa_destroy returns SQA_ERR_INVALID. */
 sqa_status pt_run(sqa_handle *h, const double *betas, int32_t n_temps, int32_t n_sweeps,
                   int32_t swap_every, void *stream);
 
@@ -221,8 +225,8 @@ sqa_status sqa_decode_bp(sqa_handle *h, double error_rate, int32_t iterations, i
 typedef struct sqa_batch sqa_batch;
 /* Plans the handles (SQA or PT, any sizes) once for one persistent launch of
  * the multi-job sweep kernel: every job's units in one list, longest first.
- * The handles must outlive the batch and must not be tuned or destroyed
- * while it exists. */
+ * The handles must outlive the batch and must not be tuned, switched to PT
+ * (pt_run) or destroyed while it exists. */
 sqa_status sqa_batch_create(sqa_handle *const *hs, int32_t n, sqa_batch **out);
 /* Asynchronous on stream: fresh initial spins for every job, then all their
  * sweeps.  The first call captures this sequence into a CUDA graph; every
@@ -237,6 +241,8 @@ sqa_status sqa_batch_launch(sqa_batch *b, void *stream);
  * rate. */
 sqa_status sqa_batch_autotune(sqa_batch *b, int32_t n_trial, void *stream, int32_t *words_per_unit,
                               double *attempts_per_s);
+/* Waits for the device (a replay may still be in flight on any stream) and
+ * frees the batch; the handles stay the caller's.  NULL is a no-op. */
 void sqa_batch_destroy(sqa_batch *b);
 /* Times h's sweep kernel in every launch shape that fits (cluster size 1, 2,
  * 4, 8, 16; table or window lookup; words per unit W, ceil(W/2), ..., 1) on

@@ -154,7 +154,11 @@ sqa_status time_on(cudaStream_t s, F fn, double *sec)
     if (st != SQA_OK) return st;
     cudaEvent_t e0, e1;
     SQA_TRY(cudaEventCreate(&e0));
-    SQA_TRY(cudaEventCreate(&e1));
+    const cudaError_t ec = cudaEventCreate(&e1);
+    if (ec != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ec, "cudaEventCreate");
+    }
     cudaEventRecord(e0, s);
     st = fn();
     cudaEventRecord(e1, s);
@@ -177,8 +181,10 @@ sqa_status sqa_batch_create(sqa_handle *const *hs, int32_t n, sqa_batch **out)
 {
     if (!hs || n < 1 || !out) return set_error("batch arguments"), SQA_ERR_INVALID;
     *out = nullptr;
-    for (int k = 0; k < n; k++)
-        if (!hs[k]) return set_error("NULL handle in batch"), SQA_ERR_INVALID;
+    for (int k = 0; k < n; k++) {
+        const sqa_status us = usable(hs[k]);
+        if (us != SQA_OK) return us;
+    }
     sqa_batch *b = new (std::nothrow) sqa_batch();
     if (!b) return SQA_ERR_NOMEM;
     b->hs.assign(hs, hs + n);
@@ -252,13 +258,19 @@ void sqa_batch_destroy(sqa_batch *b)
 sqa_status sqa_autotune(sqa_handle *h, int32_t n_trial, void *stream, int32_t *words_per_unit,
                         int32_t *use_table, int32_t *cluster, double *attempts_per_s)
 {
-    if (!h || n_trial < 1) return set_error("autotune arguments"), SQA_ERR_INVALID;
+    const sqa_status us = usable(h);
+    if (us != SQA_OK) return us;
+    if (n_trial < 1) return set_error("autotune arguments"), SQA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const int trial = std::min<int>(n_trial, h->S);
     const size_t bytes = (size_t)h->I * h->job.Z * h->job.n * h->job.W * sizeof(uint32_t);
     uint32_t *saved = nullptr;
     SQA_TRY(cudaMallocAsync((void **)&saved, bytes, s));
-    SQA_TRY(cudaMemcpyAsync(saved, h->d_state, bytes, cudaMemcpyDeviceToDevice, s));
+    const cudaError_t ecp = cudaMemcpyAsync(saved, h->d_state, bytes, cudaMemcpyDeviceToDevice, s);
+    if (ecp != cudaSuccess) {
+        cudaFreeAsync(saved, s);
+        return cuda_fail(ecp, "sqa_autotune save");
+    }
     const int keep_wc = h->force_wc, keep_mode = h->force_mode, keep_c = h->force_cluster;
     const int64_t attempts = (int64_t)h->job.n * h->job.Z * h->R * h->I * trial;
     struct Choice {

@@ -86,6 +86,13 @@ sqa_status device_ready()
     return SQA_OK;
 }
 
+sqa_status usable(const sqa_handle *h)
+{
+    if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
+    if (!h->ready) return set_error("the handle has no device program (its last setup failed)"), SQA_ERR_INVALID;
+    return SQA_OK;
+}
+
 }  // namespace sqa
 
 using namespace sqa;
@@ -121,6 +128,8 @@ sqa_status upload(sqa_handle *h, T **p, const std::vector<T> &v)
     return SQA_OK;
 }
 
+// Frees every device buffer of h in stream order on s and forgets them: h
+// runs nothing until a setup completes again.
 void free_all(sqa_handle *h, cudaStream_t s = 0)
 {
     for (void *p : h->allocs)
@@ -128,7 +137,25 @@ void free_all(sqa_handle *h, cudaStream_t s = 0)
     h->allocs.clear();
     h->device_bytes = 0;
     h->h2d_bytes = 0;
+    h->ready = false;
+    h->d_state = nullptr;
+    h->d_sites = nullptr;
+    h->d_T = nullptr;
+    h->d_eterms = nullptr;
+    h->d_ecls = nullptr;
+    h->d_Tsw = h->d_Tb = h->d_Tacc = nullptr;
+    h->d_accoff = h->d_acclen = h->d_swoff = h->d_swlen = nullptr;
+    h->d_canon = h->d_compact = nullptr;
+    h->d_J = nullptr;
+    h->d_chain = h->d_pair = nullptr;
+    h->d_parents = h->d_orders = nullptr;
+    h->cur_trees = h->cur_tree_kind = -1;
+    h->d_job = nullptr;
+    h->d_units = nullptr;
+    h->n_units = 0;
+    h->d_counter = nullptr;
 }
+
 
 // Row stride (words) of the shared state for units of wc words: consecutive
 // lanes take consecutive words, then the next z step (two slices for SQA, one
@@ -404,11 +431,14 @@ sqa_status setup_program(sqa_handle *h)
     if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) return st;
     h->n_units = (int)h->units.size();
     if ((st = dalloc(h, &h->d_counter, 1)) != SQA_OK) return st;
+    h->ready = true;
     return SQA_OK;
 }
 
 sqa_status launch_sweeps(sqa_handle *h, int t0, int t1, int u0, int nu, cudaStream_t s)
 {
+    if (!h->d_units || u0 < 0 || nu < 0 || u0 + nu > h->n_units)
+        return set_error("no unit list on the device (a failed sqa_tune)"), SQA_ERR_INVALID;
     h->job.t0 = t0;
     h->job.t1 = t1;
     SQA_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
@@ -660,7 +690,9 @@ sqa_status sqa_get_info(const sqa_handle *h, sqa_info *o)
 
 sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, int32_t cluster)
 {
-    if (!h || words_per_unit < 0 || use_table < -1 || use_table > 1 || cluster < 0 || cluster > 16 ||
+    sqa_status us = usable(h);
+    if (us != SQA_OK) return us;
+    if (words_per_unit < 0 || use_table < -1 || use_table > 1 || cluster < 0 || cluster > 16 ||
         (cluster & (cluster - 1)))
         return set_error("tune arguments"), SQA_ERR_INVALID;
     if (use_table == 0 && h->window_limit_exceeded) return set_error("window mode cannot hold this problem"), SQA_ERR_UNSUPPORTED;
@@ -684,8 +716,13 @@ sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, in
     SQA_CUDA(cudaFreeAsync(h->d_units, 0));
     for (auto &p : h->allocs)
         if (p == (void *)h->d_units) p = nullptr;
+    h->device_bytes -= (int64_t)(std::max<size_t>(keep_units.size(), 1) * sizeof(Unit));
     h->d_units = nullptr;
-    if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) return st;
+    h->n_units = 0;  // the handle runs nothing until a unit list is on the device again
+    if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) {
+        h->d_units = nullptr;
+        return st;
+    }
     h->n_units = (int)h->units.size();
     return SQA_OK;
 }
@@ -703,7 +740,9 @@ sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t 
 
 sqa_status sqa_run_sweeps(sqa_handle *h, int32_t t0, int32_t t1, void *stream)
 {
-    if (!h || t0 < 0 || t1 < t0 || t1 > h->S) return set_error("sweep range"), SQA_ERR_INVALID;
+    sqa_status us = usable(h);
+    if (us != SQA_OK) return us;
+    if (t0 < 0 || t1 < t0 || t1 > h->S) return set_error("sweep range"), SQA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     sqa_status st;
     if (t0 == 0 && (st = launch_init(h, s)) != SQA_OK) return st;
@@ -719,7 +758,8 @@ sqa_status sqa_run(sqa_handle *h, void *stream)
 
 sqa_status sqa_run_per_instance(sqa_handle *h, void *stream)
 {
-    if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
+    sqa_status us = usable(h);
+    if (us != SQA_OK) return us;
     cudaStream_t s = (cudaStream_t)stream;
     sqa_status st;
     if ((st = launch_init(h, s)) != SQA_OK) return st;
@@ -764,7 +804,7 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
     sqa_status st;
     for (int k = 0; k < n; k++) {
         sqa_handle *h = hs[k];
-        if (!h) return set_error("NULL handle in batch"), SQA_ERR_INVALID;
+        if ((st = usable(h)) != SQA_OK) return st;
         if ((st = launch_init(h, s)) != SQA_OK) return st;
         // the multi-job kernel runs every unit in one block: plan each job
         // for a single block per unit
@@ -790,19 +830,25 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
     JobDev *d_jobs = nullptr;
     Unit *d_units = nullptr;
     int *d_counter = nullptr;
-    SQA_CUDA(cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(JobDev), s));
-    SQA_CUDA(cudaMallocAsync((void **)&d_units, units.size() * sizeof(Unit), s));
-    SQA_CUDA(cudaMallocAsync((void **)&d_counter, sizeof(int), s));
-    SQA_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, s));
-    SQA_CUDA(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s));
-    SQA_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(int), s));
-    const int grid = grid_for((const void *)sweep_kernel, smem, (int)units.size());
-    sweep_kernel<<<grid, kThreads, smem, s>>>(d_jobs, d_units, (int)units.size(), d_counter);
-    SQA_CUDA(cudaGetLastError());
-    SQA_CUDA(cudaFreeAsync(d_jobs, s));
-    SQA_CUDA(cudaFreeAsync(d_units, s));
-    SQA_CUDA(cudaFreeAsync(d_counter, s));
-    // host vectors are consumed: pageable copies are staged before return
+    cudaError_t e = cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(JobDev), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_units, units.size() * sizeof(Unit), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_counter, sizeof(int), s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        const int grid = grid_for((const void *)sweep_kernel, smem, (int)units.size());
+        sweep_kernel<<<grid, kThreads, smem, s>>>(d_jobs, d_units, (int)units.size(), d_counter);
+        e = cudaGetLastError();
+    }
+    // freed in stream order after the launch (or at once on an error); host
+    // vectors are consumed: pageable copies are staged before return
+    if (d_jobs) cudaFreeAsync(d_jobs, s);
+    if (d_units) cudaFreeAsync(d_units, s);
+    if (d_counter) cudaFreeAsync(d_counter, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sqa_batch_run");
     return SQA_OK;
 }
 
@@ -815,14 +861,20 @@ static sqa_status to_out(void *dst, const void *dev_src, size_t bytes, int out_i
 
 static sqa_status canon_out(sqa_handle *h, int z0, int zc, uint32_t *out, int out_is_device, void *stream)
 {
-    if (!h || !out) return set_error("NULL argument"), SQA_ERR_INVALID;
+    sqa_status us = usable(h);
+    if (us != SQA_OK) return us;
+    if (!out) return set_error("NULL argument"), SQA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t count = (size_t)h->I * zc * h->job.n_phys * h->job.W;
     uint32_t *dst = out;
     if (!out_is_device) SQA_CUDA(cudaMallocAsync((void **)&dst, count * 4, s));
     const int blocks = (int)std::min<size_t>((count + kThreads - 1) / kThreads, 8192);
     canon_kernel<<<std::max(blocks, 1), kThreads, 0, s>>>(h->job, h->d_compact, z0, zc, dst);
-    SQA_CUDA(cudaGetLastError());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        if (!out_is_device) cudaFreeAsync(dst, s);
+        return cuda_fail(e, "canon_kernel");
+    }
     if (!out_is_device) {
         sqa_status st = to_out(out, dst, count * 4, 0, s);
         cudaFreeAsync(dst, s);
@@ -844,14 +896,20 @@ sqa_status sqa_state(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *
 
 sqa_status sqa_energies(sqa_handle *h, int32_t *out, int32_t out_is_device, void *stream)
 {
-    if (!h || !out) return set_error("NULL argument"), SQA_ERR_INVALID;
+    sqa_status us = usable(h);
+    if (us != SQA_OK) return us;
+    if (!out) return set_error("NULL argument"), SQA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t count = (size_t)h->I * h->job.Z * h->R;
     int32_t *dst = out;
     if (!out_is_device) SQA_CUDA(cudaMallocAsync((void **)&dst, count * 4, s));
     const int blocks = (int)std::min<size_t>((count + kThreads - 1) / kThreads, 8192);
     energy_kernel<<<std::max(blocks, 1), kThreads, 0, s>>>(h->job, dst);
-    SQA_CUDA(cudaGetLastError());
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        if (!out_is_device) cudaFreeAsync(dst, s);
+        return cuda_fail(e, "energy_kernel");
+    }
     if (!out_is_device) {
         sqa_status st = to_out(out, dst, count * 4, 0, s);
         cudaFreeAsync(dst, s);
@@ -886,7 +944,8 @@ static sqa_status decode_impl(sqa_handle *h, int32_t method, int32_t n_trees, do
                               int8_t *logical_out, int64_t *energy_out, const int64_t *e_ground,
                               int32_t *success_out, int32_t out_is_device, void *stream)
 {
-    if (!h) return set_error("NULL handle"), SQA_ERR_INVALID;
+    const sqa_status us = usable(h);
+    if (us != SQA_OK) return us;
     const bool me = h->emb == SQA_EMB_ME_CHIMERA;
     if (me != (method == SQA_DECODE_ME_MV) ||
         (method < SQA_DECODE_ME_MV || method > SQA_DECODE_LHZ_BP))
@@ -935,16 +994,31 @@ static sqa_status decode_impl(sqa_handle *h, int32_t method, int32_t n_trees, do
                 D.bp_dec[neg][S + h->N - 2] = (int8_t)(d > 0.0 ? 1 : (d < 0.0 ? -1 : 0));
             }
     }
+    // temporaries, freed in stream order on every return
+    struct Temps {
+        cudaStream_t s;
+        void *p[4];
+        int n;
+        ~Temps()
+        {
+            for (int i = 0; i < n; i++) cudaFreeAsync(p[i], s);
+        }
+    } tmp{s, {}, 0};
+    auto temp = [&](void **ptr, size_t bytes) {
+        const cudaError_t e = cudaMallocAsync(ptr, bytes, s);
+        if (e == cudaSuccess) tmp.p[tmp.n++] = *ptr;
+        return e;
+    };
     int8_t *d_log = logical_out;
     int64_t *d_en = energy_out, *d_eg = nullptr;
     int32_t *d_succ = success_out;
     if (!out_is_device) {
-        if (logical_out) SQA_CUDA(cudaMallocAsync((void **)&d_log, nrep * h->N, s));
-        if (energy_out) SQA_CUDA(cudaMallocAsync((void **)&d_en, nrep * 8, s));
-        if (success_out) SQA_CUDA(cudaMallocAsync((void **)&d_succ, (size_t)h->I * 4, s));
+        if (logical_out) SQA_CUDA(temp((void **)&d_log, nrep * h->N));
+        if (energy_out) SQA_CUDA(temp((void **)&d_en, nrep * 8));
+        if (success_out) SQA_CUDA(temp((void **)&d_succ, (size_t)h->I * 4));
     }
     if (e_ground) {
-        SQA_CUDA(cudaMallocAsync((void **)&d_eg, (size_t)h->I * 8, s));
+        SQA_CUDA(temp((void **)&d_eg, (size_t)h->I * 8));
         SQA_CUDA(cudaMemcpyAsync(d_eg, e_ground, (size_t)h->I * 8, cudaMemcpyHostToDevice, s));
     }
     if (d_succ) SQA_CUDA(cudaMemsetAsync(d_succ, 0, (size_t)h->I * 4, s));
@@ -960,11 +1034,7 @@ static sqa_status decode_impl(sqa_handle *h, int32_t method, int32_t n_trees, do
         if (energy_out) SQA_CUDA(cudaMemcpyAsync(energy_out, d_en, nrep * 8, cudaMemcpyDeviceToHost, s));
         if (success_out) SQA_CUDA(cudaMemcpyAsync(success_out, d_succ, (size_t)h->I * 4, cudaMemcpyDeviceToHost, s));
         SQA_CUDA(cudaStreamSynchronize(s));
-        if (logical_out) cudaFreeAsync(d_log, s);
-        if (energy_out) cudaFreeAsync(d_en, s);
-        if (success_out) cudaFreeAsync(d_succ, s);
     }
-    if (d_eg) cudaFreeAsync(d_eg, s);
     return SQA_OK;
 }
 
@@ -982,14 +1052,16 @@ sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, i
         cudaFree(dJ);
         return cuda_fail(e, "cudaMalloc");
     }
-    cudaMemcpy(dJ, J, npair * n_instances * 4, cudaMemcpyHostToDevice);
-    cudaMemset(dbest, 0xFF, (size_t)n_instances * 8);
+    e = cudaMemcpy(dJ, J, npair * n_instances * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dbest, 0xFF, (size_t)n_instances * 8);
     const int total_bits = N - 1;
     const int chunk_bits = std::max(0, std::min(total_bits, total_bits - 17));
     const int64_t n_chunks = (int64_t)1 << (total_bits - chunk_bits);
     const int bx = (int)std::min<int64_t>((n_chunks + 127) / 128, 2048);
-    ground_kernel<<<dim3(std::max(bx, 1), n_instances), 128>>>(N, dJ, chunk_bits, n_chunks, dbest);
-    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        ground_kernel<<<dim3(std::max(bx, 1), n_instances), 128>>>(N, dJ, chunk_bits, n_chunks, dbest);
+        e = cudaGetLastError();
+    }
     std::vector<unsigned long long> best(n_instances);
     if (e == cudaSuccess) e = cudaMemcpy(best.data(), dbest, (size_t)n_instances * 8, cudaMemcpyDeviceToHost);
     cudaFree(dJ);

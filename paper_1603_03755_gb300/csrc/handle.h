@@ -44,6 +44,7 @@ struct sqa_handle {
     int64_t device_bytes = 0;
     int64_t h2d_bytes = 0;
     std::vector<void *> allocs;
+    bool ready = false;  // a complete device program is resident (set by its setup)
 };
 
 
@@ -52,6 +53,9 @@ namespace sqa {
 constexpr int kThreads = 256;  // threads per block of every kernel here
 
 sqa_status device_ready();
+// SQA_OK when h holds a complete device program (else SQA_ERR_INVALID: NULL,
+// or its last setup failed part way, e.g. a rejected pt_run).
+sqa_status usable(const sqa_handle *h);
 void set_error(const std::string &msg);
 sqa_status cuda_fail(cudaError_t e, const char *where);
 // Draws fresh initial spins for every instance of h on stream s.

@@ -90,7 +90,8 @@ void fail_job(sqa_server *s, Job *j, sqa_status st)
     s->cv_done.notify_all();
 }
 
-// Launches the chunk of j's sweeps that starts at j->t_next, on j's stream.
+// Launches the chunk of j's sweeps that starts at j->t_next, on j's stream
+// (the caller counts it in the stats under s->mu).
 sqa_status launch_chunk(sqa_server *s, Job *j)
 {
     sqa_handle *h = j->h;
@@ -105,7 +106,6 @@ sqa_status launch_chunk(sqa_server *s, Job *j)
     if (e == cudaSuccess) e = cudaEventRecord(j->done, st);
     if (e != cudaSuccess) return cuda_fail(e, "server chunk");
     j->t_chunk_end = J.t1;
-    s->stats.chunks++;
     return SQA_OK;
 }
 
@@ -176,6 +176,7 @@ void admit(sqa_server *s)
             fail_job(s, j, st);
             continue;
         }
+        s->stats.chunks++;
         s->active.push_back(j);
         s->stats.max_resident = std::max<int64_t>(s->stats.max_resident, (int64_t)s->active.size());
         s->stats.max_bytes = std::max(s->stats.max_bytes, s->used);
@@ -231,6 +232,10 @@ sqa_status advance(sqa_server *s, bool *progressed)
         j->t_next = j->t_chunk_end;
         if (j->t_next < h->S) {
             status = launch_chunk(s, j);
+            if (status == SQA_OK) {
+                std::lock_guard<std::mutex> lock(s->mu);
+                s->stats.chunks++;
+            }
             keep.push_back(j);
         } else {
             retire(s, j);
@@ -258,8 +263,11 @@ void worker_loop(sqa_server *s)
         bool progressed = false;
         const sqa_status st = advance(s, &progressed);
         const auto c2 = std::chrono::steady_clock::now();
-        s->stats.admit_s += std::chrono::duration<double>(c1 - c0).count();
-        s->stats.advance_s += std::chrono::duration<double>(c2 - c1).count();
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->stats.admit_s += std::chrono::duration<double>(c1 - c0).count();
+            s->stats.advance_s += std::chrono::duration<double>(c2 - c1).count();
+        }
         if (st != SQA_OK) {
             // a launch or a chunk failed: fail every resident job
             for (int q = 0; q < kPoolStreams; q++) cudaStreamSynchronize(s->pool[q]);

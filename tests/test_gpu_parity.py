@@ -256,6 +256,46 @@ def test_mwd_decode_of_pt_readouts_k16():
     h.close()
 
 
+def test_failed_pt_switch_leaves_no_program():
+    """pt_run releases the handle's SQA program before it builds the PT one;
+    couplings too large for PT's byte-wise windows (penalty 60) are refused
+    there, and every later call but close must raise instead of launching on
+    released memory."""
+    J = W.random_instances(8, 2, 5)
+    h = pkg.Handle(embedding="me", N=8, J=J, penalty=60, sweeps=10, R=32, seed=5, L=8, beta=1.0)
+    h.run(stream=0)
+    with pytest.raises(pkg.SQAError) as e:
+        h.pt_run(W.geometric_ladder(4, 2.0, 0.5), 10, 1, stream=0)
+    assert e.value.status == pkg.SQA_ERR_UNSUPPORTED
+    for call in (lambda: h.run(stream=0), lambda: h.run_sweeps(0, 5, stream=0), lambda: h.readout(stream=0),
+                 lambda: h.state(stream=0), lambda: h.energies(stream=0), lambda: h.decode("me_mv", 0, stream=0),
+                 lambda: h.tune(1, 1, 1)):
+        with pytest.raises(pkg.SQAError) as e:
+            call()
+        assert e.value.status == pkg.SQA_ERR_INVALID
+    h.close()
+
+
+def test_tree_decode_after_switch_to_pt():
+    """Decoding trees cached by an SQA program are released with it: after a
+    switch to PT the same decode equals a fresh PT handle's."""
+    N, R, S = 7, 64, 30
+    J = W.random_instances(N, 2, 21)
+    betas = W.geometric_ladder(6, 5.0, 0.5)
+    h = pkg.Handle(embedding="lhz", N=N, J=J, penalty=9, sweeps=S, R=R, seed=21, L=8, beta=1.0)
+    h.run(stream=0)
+    h.decode("lhz_trees", 3, stream=0)
+    h.pt_run(betas, S, 1, stream=0)
+    got = h.decode("lhz_trees", 3, stream=0)
+    h.close()
+    f = pkg.Handle(embedding="lhz", N=N, J=J, penalty=9, sweeps=S, R=R, seed=21, kind="pt", betas=betas,
+                   swap_every=1)
+    f.run(stream=0)
+    want = f.decode("lhz_trees", 3, stream=0)
+    f.close()
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+
+
 @pytest.mark.parametrize("N", [2, 3, 5, 8, 11, 16])
 def test_ground_energy_parity(N):
     J = W.random_instances(N, 4, 50 + N)
