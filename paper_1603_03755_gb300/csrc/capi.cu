@@ -276,6 +276,15 @@ sqa_status validate(const sqa_desc *d)
     if (d->n_instances < 1 || !d->J) return set_error("n_instances / J"), SQA_ERR_INVALID;
     if (d->penalty <= 0) return set_error("penalty must be > 0"), SQA_ERR_INVALID;
     if (d->n_sweeps < 1 || d->n_replicas < 1) return set_error("n_sweeps / n_replicas"), SQA_ERR_INVALID;
+    {
+        // bound the magnitudes before any per-site sum is formed (the exact
+        // limit, a site's weight sum within the int16 records, comes later)
+        const int32_t lim = 1 << 24;
+        if (d->penalty > lim) return set_error("penalty too large"), SQA_ERR_UNSUPPORTED;
+        const int64_t npair = (int64_t)d->n_logical * (d->n_logical - 1) / 2;
+        for (int64_t i = 0; i < (int64_t)d->n_instances * npair; i++)
+            if (d->J[i] > lim || d->J[i] < -lim) return set_error("couplings too large"), SQA_ERR_UNSUPPORTED;
+    }
     if (d->h) {
         for (int64_t i = 0; i < (int64_t)d->n_instances * d->n_logical; i++)
             if (d->h[i] != 0) return set_error("non-zero logical fields need an ancilla"), SQA_ERR_UNSUPPORTED;

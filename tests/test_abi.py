@@ -169,6 +169,12 @@ def test_validation_before_device_work(L):
     d, keep = _desc("sqa", "lhz", 6, J, 9, 10, L=130)
     d.move = 1                                                # cluster moves need L <= 128
     assert L.sqa_create(C.byref(d), C.byref(h)) == pkg.SQA_ERR_UNSUPPORTED
+    Jbig = J.copy()
+    Jbig[3] = np.iinfo(np.int32).min                          # |J| beyond any site sum
+    d, keep = _desc("sqa", "me", 6, Jbig, 6, 10)
+    assert L.sqa_create(C.byref(d), C.byref(h)) == pkg.SQA_ERR_UNSUPPORTED
+    d, keep = _desc("sqa", "me", 6, J, 1 << 25, 10)          # penalty beyond any site sum
+    assert L.sqa_create(C.byref(d), C.byref(h)) == pkg.SQA_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("emb,N,S,Ls,beta", [("me", 8, 40, 64, 10 / 3), ("lhz", 6, 30, 16, 1.0)])
