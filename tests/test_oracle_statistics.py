@@ -8,7 +8,9 @@ P5  SQA at a frozen (A, B) samples the exact Trotterised path distribution
     enumerated over every path (chi-square); a wrong sign of Jperp is rejected.
 P6  SQA at large L approaches the quantum thermal state: the single-spin
     closed form <sigma^z> = -(B J / w) tanh(beta w), w = sqrt(A^2 + B^2 J^2),
-    and an exact diagonalisation (numpy) of a 4-spin transverse-field problem.
+    and an exact diagonalisation (numpy) of a 4-spin transverse-field problem;
+    at small L it matches the exact finite-L Trotter value from the transfer
+    matrix (whose error against the limit falls as (beta / L)^2).
 P8  PT with two slots and swaps samples the product of the two Boltzmann
     distributions (chi-square over the joint histogram).
 P3  PT on the paper's ladder down to beta = 20 finds the logical ground state.
@@ -209,6 +211,64 @@ def test_p6_exact_diagonalisation_me_k2():
     classical = float((_boltzmann(diagE, beta * B0) * diagE).sum())
     assert abs(est - exact) < 0.05 * abs(exact) + 0.05, (est, exact)
     assert abs(classical - exact) > 3 * abs(est - exact)
+
+
+def _trotter_expectation(diagE, m, beta, A0, B0, L):
+    """<E_P> of the L-slice Trotter decomposition of exp(-beta H),
+    H = B0 diag(E) - A0 sum_i sigma^x_i, as the trace of the transfer matrix
+    sqrt(D) K sqrt(D) to the power L: D = diag(exp(-beta B0 E / L)) and
+    K = exp((beta A0 / L) sigma^x) on every spin (cosh / sinh entries), built
+    from the matrix exponential, not from a coupling along imaginary time."""
+    a = beta * A0 / L
+    k1 = np.array([[math.cosh(a), math.sinh(a)], [math.sinh(a), math.cosh(a)]])
+    K = np.ones((1, 1))
+    for _ in range(m):
+        K = np.kron(K, k1)
+    d = np.exp(-beta * B0 * (diagE - diagE.min()) / (2 * L))
+    ML = np.linalg.matrix_power(d[:, None] * K * d[None, :], L)
+    return float(np.trace(np.diag(diagE) @ ML) / np.trace(ML))
+
+
+def _thermal_expectation(diagE, m, beta, A0, B0):
+    dim = 2 ** m
+    H = np.diag(B0 * diagE)
+    for b in range(m):
+        for k in range(dim):
+            H[k ^ (1 << b), k] -= A0
+    ev, V = np.linalg.eigh(H)
+    rho = V @ np.diag(np.exp(-beta * (ev - ev.min()))) @ V.T
+    return float(np.trace(np.diag(diagE) @ rho) / np.trace(rho))
+
+
+def test_p6_finite_trotter_number_transfer_matrix():
+    """ME of K_2 (4 spins, 4 L path bits: too many to enumerate at L = 8) at a
+    frozen (A, B) where the Trotter error is large: the oracle's <H_P> at
+    L = 4 and 8 equals the transfer-matrix value of that L, which differs from
+    the other L and from the quantum limit by far more than the tolerance.
+    The transfer matrices themselves approach exact diagonalisation with an
+    error falling as (beta / L)^2."""
+    pb = O.Problem("me", 2, np.array([2], np.int32), 1)
+    states, used = _all_states(pb)
+    diagE = _energy_np(pb, states).astype(np.float64)
+    m = len(used)
+    beta, A0, B0 = 3.0, 1.0, 0.6
+    exact = {L: _trotter_expectation(diagE, m, beta, A0, B0, L) for L in (4, 8, 16, 32, 512)}
+    limit = _thermal_expectation(diagE, m, beta, A0, B0)
+    assert abs(exact[512] - limit) < 1e-3
+    r = (exact[16] - limit) / (exact[32] - limit)
+    assert 3.6 < r < 4.4, r                       # Trotter error ~ (beta / L)^2
+    for L in (4, 8):
+        S = 1600
+        q = O.SQA(pb, L, 256, beta, np.full(S, A0), np.full(S, B0), seed=40 + L)
+        q.run(0, 100)
+        acc = []
+        for t in range(100, S, 6):
+            q.run(t, t + 6)
+            acc.append(q.slice_energies().mean())
+        est = float(np.mean(acc))
+        assert abs(est - exact[L]) < 0.03, (L, est, exact[L])
+        others = [exact[k] for k in (4, 8, 16) if k != L] + [limit]
+        assert min(abs(est - o) for o in others) > 0.12, (L, est, others)
 
 
 def test_p8_pt_two_slot_joint_distribution():
