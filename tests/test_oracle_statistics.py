@@ -213,8 +213,8 @@ def test_p6_exact_diagonalisation_me_k2():
     assert abs(classical - exact) > 3 * abs(est - exact)
 
 
-def _trotter_expectation(diagE, m, beta, A0, B0, L):
-    """<E_P> of the L-slice Trotter decomposition of exp(-beta H),
+def _trotter_expectation(diagE, m, beta, A0, B0, L, obs=None):
+    """<E_P> (or <obs>, diagonal) of the L-slice Trotter decomposition of exp(-beta H),
     H = B0 diag(E) - A0 sum_i sigma^x_i, as the trace of the transfer matrix
     sqrt(D) K sqrt(D) to the power L: D = diag(exp(-beta B0 E / L)) and
     K = exp((beta A0 / L) sigma^x) on every spin (cosh / sinh entries), built
@@ -226,7 +226,8 @@ def _trotter_expectation(diagE, m, beta, A0, B0, L):
         K = np.kron(K, k1)
     d = np.exp(-beta * B0 * (diagE - diagE.min()) / (2 * L))
     ML = np.linalg.matrix_power(d[:, None] * K * d[None, :], L)
-    return float(np.trace(np.diag(diagE) @ ML) / np.trace(ML))
+    o = diagE if obs is None else obs
+    return float(np.trace(np.diag(o) @ ML) / np.trace(ML))
 
 
 def _thermal_expectation(diagE, m, beta, A0, B0):
@@ -244,9 +245,10 @@ def test_p6_finite_trotter_number_transfer_matrix():
     """ME of K_2 (4 spins, 4 L path bits: too many to enumerate at L = 8) at a
     frozen (A, B) where the Trotter error is large: the oracle's <H_P> at
     L = 4 and 8 equals the transfer-matrix value of that L, which differs from
-    the other L and from the quantum limit by far more than the tolerance.
-    The transfer matrices themselves approach exact diagonalisation with an
-    error falling as (beta / L)^2."""
+    the other L and from the quantum limit by far more than the tolerance, and
+    at L = 8 so does <sigma^z_a sigma^z_b> for every pair of spins.  The
+    transfer matrices themselves approach exact diagonalisation with an error
+    falling as (beta / L)^2."""
     pb = O.Problem("me", 2, np.array([2], np.int32), 1)
     states, used = _all_states(pb)
     diagE = _energy_np(pb, states).astype(np.float64)
@@ -257,18 +259,28 @@ def test_p6_finite_trotter_number_transfer_matrix():
     assert abs(exact[512] - limit) < 1e-3
     r = (exact[16] - limit) / (exact[32] - limit)
     assert 3.6 < r < 4.4, r                       # Trotter error ~ (beta / L)^2
+    pairs = [(a, b) for a in range(m) for b in range(a + 1, m)]
+    corr = {(a, b): states[:, used[a]].astype(np.float64) * states[:, used[b]] for a, b in pairs}
     for L in (4, 8):
         S = 1600
         q = O.SQA(pb, L, 256, beta, np.full(S, A0), np.full(S, B0), seed=40 + L)
         q.run(0, 100)
-        acc = []
+        acc, cacc = [], []
         for t in range(100, S, 6):
             q.run(t, t + 6)
             acc.append(q.slice_energies().mean())
+            sz = q.s.astype(np.float64)
+            cacc.append([(sz[:, used[a], :] * sz[:, used[b], :]).mean() for a, b in pairs])
         est = float(np.mean(acc))
         assert abs(est - exact[L]) < 0.03, (L, est, exact[L])
         others = [exact[k] for k in (4, 8, 16) if k != L] + [limit]
         assert min(abs(est - o) for o in others) > 0.12, (L, est, others)
+        if L == 8:
+            got = np.mean(cacc, axis=0)
+            want = np.array([_trotter_expectation(diagE, m, beta, A0, B0, 8, corr[p]) for p in pairs])
+            far = np.array([_trotter_expectation(diagE, m, beta, A0, B0, 512, corr[p]) for p in pairs])
+            assert np.abs(got - want).max() < 0.03, (got, want)
+            assert np.abs(got - far).max() > 0.06, (got, far)
 
 
 def test_p8_pt_two_slot_joint_distribution():
