@@ -13,19 +13,24 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import threading
 
 import numpy as np
 
 from . import build as _build
 
 _lib = None
+_lib_lock = threading.Lock()
 
 
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
-        _declare(_lib)
+        with _lib_lock:  # threads of one process build and load it once
+            if _lib is None:
+                L = C.CDLL(_build.build())
+                _declare(L)
+                _lib = L
     return _lib
 
 

@@ -12,6 +12,7 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ("philox.c", "embed.c", "anneal.c", "decode.c")
@@ -31,7 +32,7 @@ def build(force: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = LIB + f".tmp{os.getpid()}.{threading.get_ident()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
            "-fno-fast-math", "-Wall", "-Wextra", "-Wno-unused-parameter", "-o", tmp]
     cmd += [os.path.join(HERE, s) for s in SOURCES]
