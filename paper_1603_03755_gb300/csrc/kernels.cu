@@ -17,10 +17,12 @@
 //
 // Per item (site, z, word) the single-spin sweep draws the item's four
 // Philox blocks (16 high uniform bits per replica), forms for each term of
-// the site the word of replicas whose term value is negative (and, for SQA,
-// the two temporal disagreement words), turns them into one threshold index
-// per replica (a per-site code table after an 8x8 bit-matrix transpose, or
-// byte-wise sums into the site's window of the threshold row), and compares
+// the site the word of replicas whose term value is negative (code tables:
+// whose spin product is -1, the table folding in the weight's sign) and, for
+// SQA, the two temporal disagreement words, turns them into one threshold
+// index per replica (a per-site code table after an 8x8 bit-matrix
+// transpose, or byte-wise sums into the site's window of the threshold
+// row), and compares
 // the uniforms' high halves with the thresholds' through the carry of a
 // subtraction; only a tie of the high halves draws the low half
 // (probability 2^-16).  PT recounts energies for its swaps in bit-sliced
@@ -134,10 +136,12 @@ __device__ __forceinline__ uint32_t sub_carry_into(uint32_t x, uint32_t q, uint3
 }
 
 // Term planes of one item: bit b of pl[k] is set when term k's value is
-// negative for replica b (it turns positive on a flip).  kw[k] is K*|w_k|.
+// negative for replica b (it turns positive on a flip); without SIGN, when
+// the product of the term's spins is -1 (the per-site code tables fold the
+// weight's sign in, so the item never loads the weights).  kw[k] is K*|w_k|.
 // PAIRS: every term has exactly one other member (minor embedding);
 // otherwise absent members read the zero word of site n (branch-free).
-template <bool PAIRS>
+template <bool PAIRS, bool SIGN = true>
 __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *row, int n, int wc, int w,
                                             uint32_t s, uint32_t (&pl)[kMaxTerms],
                                             uint32_t (&kw)[kMaxTerms])
@@ -158,10 +162,14 @@ __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *r
                 p ^= row[min((uint32_t)(int)tr.p[1], z) * wc + w];
                 p ^= row[min((uint32_t)(int)tr.p[2], z) * wc + w];
             }
-            const int wv = tr.w;
-            // w * prod(sigma) is negative iff (product is -1) xor (w < 0)
-            pl[k] = p ^ (uint32_t)(wv >> 31);
-            kw[k] = (uint32_t)(wv < 0 ? -wv : wv);
+            if (SIGN) {
+                const int wv = tr.w;
+                // w * prod(sigma) is negative iff (product is -1) xor (w < 0)
+                pl[k] = p ^ (uint32_t)(wv >> 31);
+                kw[k] = (uint32_t)(wv < 0 ? -wv : wv);
+            } else {
+                pl[k] = p;
+            }
         }
     }
 }
@@ -230,18 +238,26 @@ struct Keys {
 };
 
 // Full threshold index of a replica from its code (SQA tables: bit 0, 1 = the
-// two temporal disagreements, bit 2+k = term k negative) or its window byte.
-template <int KIND>
+// two temporal disagreements, bit 2+k = term k negative; FOLD: bit 2+k = the
+// product of term k's spins is -1, so term k is negative when that bit
+// differs from the weight's sign bit) or its window byte.
+template <int KIND, bool FOLD = false>
 __device__ __forceinline__ int full_index(const SiteRec &sr, uint32_t code)
 {
     if (KIND == SQA_KIND_SQA) {
         int U = 2 - (int)(code & 1u) - (int)((code >> 1) & 1u);
 #pragma unroll
-        for (int k = 0; k < kMaxTerms; k++)
-            if (k < sr.nterm && ((code >> (k + 2)) & 1u)) {
+        for (int k = 0; k < kMaxTerms; k++) {
+            if (FOLD) {
+                if (k < sr.nterm) {
+                    const int wv = sr.t[k].w;
+                    if (((code >> (k + 2)) & 1u) ^ (uint32_t)(wv < 0)) U += wv < 0 ? -wv : wv;
+                }
+            } else if (k < sr.nterm && ((code >> (k + 2)) & 1u)) {
                 const int wv = sr.t[k].w;
                 U += wv < 0 ? -wv : wv;
             }
+        }
         return sr.base + U;
     }
     return sr.base + (int)code;
@@ -250,7 +266,7 @@ __device__ __forceinline__ int full_index(const SiteRec &sr, uint32_t code)
 // One item: the word of 32 replicas of site si at local slice/slot zl.  Byte r
 // of code[j] selects replica j + 8r's threshold: a per-site table entry (SQA,
 // table mode) or an index in the site's window of the threshold row.
-template <int KIND, bool LUT, bool PAIRS = false>
+template <int KIND, bool LUT, bool PAIRS = false, bool FOLD = false>
 __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const Smem &sm, const Part &pt,
                                            int inst, int w0, int wc, int t, int si, int zl, int w)
 {
@@ -262,7 +278,7 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
     uint32_t code[8];
     {
         uint32_t pl[kMaxTerms], kw[kMaxTerms];
-        term_planes<PAIRS>(sr, row, J.n, wc, w, s, pl, kw);
+        term_planes<PAIRS, !FOLD>(sr, row, J.n, wc, w, s, pl, kw);
         uint32_t d1 = 0u, d2 = 0u;
         if (KIND == SQA_KIND_SQA) {
             // temporal disagreements: m = sigma (sigma_up + sigma_dn) = 2 - 2 (d1 + d2)
@@ -338,7 +354,7 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
                     const uint32_t sh = 16u * (uint32_t)(j & 1);
                     uint32_t u = ((aw >> sh) & 0xFFFFu) << 16 | ((word_of(B2, j >> 1) >> sh) & 0xFFFFu);
                     u = u < 0xFFFFFFFEu ? u : 0xFFFFFFFEu;
-                    const uint32_t T = Tfull[LUT ? full_index<KIND>(sr, c) : sr.base + (int)c];
+                    const uint32_t T = Tfull[LUT ? full_index<KIND, FOLD>(sr, c) : sr.base + (int)c];
                     const uint32_t bit = 1u << (8 * r + j);
                     if (u < T)
                         rej &= ~bit;
@@ -352,15 +368,18 @@ __device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const
 }
 
 // SQA: per-site tables for sweep t from the staged threshold row: entry c is
-// the high half (T & 0xFFFF0000) of T[base + 2 + sum of K|w_k| over set term bits
-// - the two temporal bits].
+// the high half (T & 0xFFFF0000) of T[base + 2 + sum of K|w_k| over the
+// negative terms - the two temporal bits], term k negative when code bit 2+k
+// is set (FOLD: when it, the spin product being -1, differs from the sign of
+// w_k).
+template <bool FOLD>
 __device__ void build_luts(const JobDev &J, const Smem &sm)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int si = warp; si < J.n; si += nw) {
         const SiteRec &sr = sm.sites[si];
         const int ne = 1 << (sr.nterm + 2);
-        for (int c = lane; c < ne; c += 32) sm.lut[sr.lut_off + c] = high_part(sm.T[full_index<SQA_KIND_SQA>(sr, (uint32_t)c)]);
+        for (int c = lane; c < ne; c += 32) sm.lut[sr.lut_off + c] = high_part(sm.T[full_index<SQA_KIND_SQA, FOLD>(sr, (uint32_t)c)]);
     }
 }
 
@@ -800,7 +819,7 @@ __device__ void run_unit_wolff(const JobDev &J, const Smem &sm, const Unit &u)
     __syncthreads();
 }
 
-template <int KIND, bool LUT, bool PAIRS = false>
+template <int KIND, bool LUT, bool PAIRS = false, bool FOLD = false>
 __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 {
     const int nthr = blockDim.x, tid = threadIdx.x;
@@ -850,7 +869,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
             }
             __syncthreads();
             if (LUT) {
-                build_luts(J, sm);
+                build_luts<FOLD>(J, sm);
                 __syncthreads();
             }
             const int half = zr >> 1;
@@ -861,7 +880,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 for (int it = tid; it < nitems; it += nthr) {
                     const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
                     const int q = (int)fdiv((uint32_t)r, div_z), zh = r - q * half;
-                    sweep_item<SQA_KIND_SQA, LUT, PAIRS>(J, K, sm, pt, inst, w0, wc, t, c0 + q, 2 * zh + par, w);
+                    sweep_item<SQA_KIND_SQA, LUT, PAIRS, FOLD>(J, K, sm, pt, inst, w0, wc, t, c0 + q, 2 * zh + par, w);
                 }
                 cluster_barrier(pt.C);  // neighbouring blocks read this phase's boundary slices
             }
@@ -894,7 +913,10 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 // four (64 registers, no spills); PT runs two blocks of 384 threads (a PT
 // job usually has one unit per ladder, fewer units than block slots, so
 // wider blocks give the busy SMs more warps).  Units go to clusters in turn (all units of a job
-// cost the same).
+// cost the same).  The two-spin-term table path (5) folds the weights' signs
+// into its code tables (FOLD): the items never load the weights.  Measured,
+// that helps this path (+3.8 %) and hurts the general-term path (-1.4 %) and
+// the multi-job kernel (-14 %), which keep term-value codes.
 template <int MODE>
 __global__ void __launch_bounds__(MODE == 0 || MODE == 6 ? 384 : 256, MODE == 3 ? 4 : (MODE == 0 || MODE == 6 ? 2 : 3))
     sweep_kernel_one(const __grid_constant__ JobDev J, const Unit *units, int n_units, int *counter)
@@ -912,7 +934,7 @@ __global__ void __launch_bounds__(MODE == 0 || MODE == 6 ? 384 : 256, MODE == 3 
         else if (MODE == 2)
             run_unit<SQA_KIND_SQA, true>(J, sm, u);
         else if (MODE == 5)
-            run_unit<SQA_KIND_SQA, true, true>(J, sm, u);
+            run_unit<SQA_KIND_SQA, true, true, true>(J, sm, u);
         else if (MODE == 3)
             run_unit_wolff<2>(J, sm, u);
         else if (MODE == 4)
