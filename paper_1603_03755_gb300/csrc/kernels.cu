@@ -378,8 +378,25 @@ __device__ void build_luts(const JobDev &J, const Smem &sm)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int si = warp; si < J.n; si += nw) {
         const SiteRec &sr = sm.sites[si];
-        const int ne = 1 << (sr.nterm + 2);
-        for (int c = lane; c < ne; c += 32) sm.lut[sr.lut_off + c] = high_part(sm.T[full_index<SQA_KIND_SQA, FOLD>(sr, (uint32_t)c)]);
+        const int nt = sr.nterm, base = sr.base, off = sr.lut_off;
+        // the site's weights once, in registers (entries are independent)
+        int aw[kMaxTerms];
+        uint32_t flip[kMaxTerms];
+#pragma unroll
+        for (int k = 0; k < kMaxTerms; k++) {
+            const int wv = k < nt ? (int)sr.t[k].w : 0;
+            aw[k] = wv < 0 ? -wv : wv;
+            flip[k] = FOLD ? (uint32_t)(wv < 0) : 0u;
+        }
+        const int ne = 1 << (nt + 2);
+        for (int c = lane; c < ne; c += 32) {
+            // as full_index: bits of terms k >= nt are 0 and their weights 0
+            int U = 2 - (c & 1) - ((c >> 1) & 1);
+#pragma unroll
+            for (int k = 0; k < kMaxTerms; k++)
+                if ((((uint32_t)c >> (k + 2)) & 1u) ^ flip[k]) U += aw[k];
+            sm.lut[off + c] = high_part(sm.T[base + U]);
+        }
     }
 }
 
@@ -914,9 +931,10 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 // job usually has one unit per ladder, fewer units than block slots, so
 // wider blocks give the busy SMs more warps).  Units go to clusters in turn (all units of a job
 // cost the same).  The two-spin-term table path (5) folds the weights' signs
-// into its code tables (FOLD): the items never load the weights.  Measured,
-// that helps this path (+3.8 %) and hurts the general-term path (-1.4 %) and
-// the multi-job kernel (-14 %), which keep term-value codes.
+// into its code tables (FOLD): the items never load the weights.  Measured
+// against term-value codes: +4.7 % on this path, while folding on the
+// general-term path and in the multi-job kernel ran 0.6 % and 2.8 % slower,
+// so they keep term-value codes.
 template <int MODE>
 __global__ void __launch_bounds__(MODE == 0 || MODE == 6 ? 384 : 256, MODE == 3 ? 4 : (MODE == 0 || MODE == 6 ? 2 : 3))
     sweep_kernel_one(const __grid_constant__ JobDev J, const Unit *units, int n_units, int *counter)
