@@ -67,8 +67,10 @@ def parse():
     ap.add_argument("--pt-only", choices=["me", "lhz"],
                     help="time only the PT workload on this embedding (a small case for profiling)")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-only", type=float, default=0.0, metavar="CAPACITY",
-                    help="run only the serving stream, offered loads relative to CAPACITY attempts/s")
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
+    ap.add_argument("--serving-capacity", type=float, default=0.0, metavar="ATTEMPTS_PER_S",
+                    help="offered loads relative to this rate (default: the server's saturated rate on the "
+                         "same job stream, measured first)")
     ap.add_argument("--serving-jobs", type=int, default=200)
     return ap.parse_args()
 
@@ -264,7 +266,7 @@ def extra_workloads(pkg, stream, args):
     out["wolff_me"] = wolff_workload(pkg, stream, args)
     out["penalty_scans"] = scan_workloads(pkg, stream, args)
     if not args.no_serving:
-        out["serving"] = [serving_workload(pkg, args.capacity, load, args.serving_jobs) for load in (0.5, 0.8, 0.95)]
+        out.update(serving_suite(pkg, args))
     return out
 
 
@@ -349,6 +351,49 @@ def job_attempts(j) -> int:
     return n * Z * j["R"] * j["sweeps"]
 
 
+def _job_kw(j):
+    kw = {k: j[k] for k in ("embedding", "N", "J", "penalty", "sweeps", "R", "seed", "kind")}
+    if j["kind"] == "sqa":
+        kw.update(L=j["L"], beta=j["beta"])
+    else:
+        kw.update(betas=j["betas"], swap_every=j["swap_every"])
+    return kw
+
+
+def serving_saturation(pkg, n_jobs=200, seed=0):
+    """The server's capacity on the serving job stream: every job submitted
+    at once (all resident if memory allows), capacity = the stream's
+    attempts / makespan."""
+    jobs = W.serving_stream(n_jobs, seed)
+    att = np.array([job_attempts(j) for j in jobs], float)
+    srv = pkg.Server(64 << 30)
+    ids = [srv.submit(**_job_kw(j)) for j in jobs]
+    for jid in ids:
+        srv.wait(jid, timeout=900)
+    infos = [srv.poll(jid) for jid in ids]
+    st = srv.stats()
+    srv.close()
+    t_first = min(i["t_submit"] for i in infos)
+    span = max(i["t_done"] for i in infos) - t_first
+    done = np.array([i["state"] == "done" for i in infos])
+    ends = np.array([i["t_done"] - t_first for i in infos])
+    return {"jobs": n_jobs, "jobs_done": int(done.sum()), "attempts": float(att.sum()),
+            "attempts_per_s": float(att[done].sum() / span), "makespan_s": span,
+            "p50_done_s": float(np.percentile(ends, 50)), "p99_done_s": float(np.percentile(ends, 99)),
+            "max_resident_jobs": st["max_resident"], "chunks": st["chunks"]}
+
+
+def serving_suite(pkg, args):
+    """Saturated capacity first, then Poisson streams at 50 / 80 / 95 % of it
+    (or of --serving-capacity)."""
+    sat = serving_saturation(pkg, args.serving_jobs)
+    cap = args.serving_capacity if args.serving_capacity > 0 else sat["attempts_per_s"]
+    loads = [serving_workload(pkg, cap, load, args.serving_jobs) for load in (0.5, 0.8, 0.95)]
+    return {"serving_capacity": dict(sat, basis="measured saturation" if args.serving_capacity <= 0
+                                     else "--serving-capacity"),
+            "serving": loads}
+
+
 def serving_workload(pkg, capacity, load, n_jobs=200, seed=0):
     """Poisson stream of SQA/PT jobs (ME or LHZ, N 6-40, L 16-128, sweeps
     log-uniform 1e3-1e5, 1-256 replicas) at `load` x capacity attempts/s,
@@ -367,11 +412,7 @@ def serving_workload(pkg, capacity, load, n_jobs=200, seed=0):
         delay = t0 + t_next - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        kw = {k: j[k] for k in ("embedding", "N", "J", "penalty", "sweeps", "R", "seed", "kind")}
-        if j["kind"] == "sqa":
-            kw.update(L=j["L"], beta=j["beta"])
-        else:
-            kw.update(betas=j["betas"], swap_every=j["swap_every"])
+        kw = _job_kw(j)
         ids.append(srv.submit(**kw))
         kws.append(kw)
     infos = []
@@ -394,8 +435,8 @@ def serving_workload(pkg, capacity, load, n_jobs=200, seed=0):
     qwait = np.array([i["t_start"] - i["t_submit"] for i in infos])
     span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
     done = [i["state"] == "done" for i in infos]
-    return {"offered_load": load, "jobs": n_jobs, "jobs_done": int(sum(done)),
-            "arrival_rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
+    return {"offered_load": load, "offered_attempts_per_s": load * capacity, "jobs": n_jobs,
+            "jobs_done": int(sum(done)), "arrival_rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "p50_queue_s": float(np.percentile(qwait, 50)),
             "attempts_per_s": float(att[np.array(done)].sum() / span), "makespan_s": span,
             "chunks": st["chunks"], "max_resident_jobs": st["max_resident"],
@@ -471,7 +512,7 @@ def main():
             print(json.dumps({"pt_only": res}))
         return
     if args.serving_only:
-        res = [serving_workload(pkg, args.serving_only, load, args.serving_jobs) for load in (0.5, 0.8, 0.95)]
+        res = serving_suite(pkg, args)
         if rank == 0:
             print(json.dumps({"serving_only": res}))
         return
@@ -592,7 +633,6 @@ def main():
     t_sweep = statistics.mean(sweep_times)
     achieved_gops = attempts * OPS_PER_ATTEMPT / t_sweep / 1e9
     traffic, traffic_note = kernel_traffic(I)
-    args.capacity = value / world
     extra = None if args.no_extra else extra_workloads(pkg, stream, args)
     cpu = None
     if not args.no_cpu_baseline:
@@ -622,9 +662,11 @@ def main():
                               "batched_over_per_instance": value / world / per_inst_rate},
         "peaks_source": src,
         "other_workloads": extra,
-        "latency": None if not extra or "serving" not in extra else {
-            f"load_{int(100 * x['offered_load'])}pct": {"p50_s": x["p50_latency_s"], "p99_s": x["p99_latency_s"]}
-            for x in extra["serving"]},
+        "latency": None if not extra or "serving" not in extra else dict(
+            {f"load_{int(100 * x['offered_load'])}pct": {"p50_s": x["p50_latency_s"], "p99_s": x["p99_latency_s"]}
+             for x in extra["serving"]},
+            loads_relative_to={"attempts_per_s": extra["serving_capacity"]["attempts_per_s"],
+                               "basis": extra["serving_capacity"]["basis"]}),
         "launch": dict(h.launch(), autotune_trial_attempts_per_s=tuned["trial_attempts_per_s"]),
     }
     print(json.dumps(out))
