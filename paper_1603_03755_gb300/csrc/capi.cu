@@ -203,7 +203,20 @@ int blocks_per_sm(const void *kernel, int smem, int threads = kThreads)
 // blocks at 90 % (barriers and remote reads); then smaller C, table mode,
 // more words per unit.  c_forced > 0 restricts C.  Writes J's shape fields
 // and the unit list.
-sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> &units)
+// Relative costs behind the planner's choice between per-site code tables
+// and byte-wise windows, in units of one table-mode item (32 attempts):
+// measured, a window-mode item costs about 1.25 of them, and rebuilding one
+// table entry (once per sweep in every block) about 0.15.  On the 1024 x 256
+// ME K_8 workload (12288 items per block per sweep, ~1200 entries) tables
+// run 1.4x faster; on 8-block clusters of single-instance jobs, with few
+// items per block, windows ran 6-70 % faster in every case measured.
+constexpr double kWindowItem = 1.25;
+constexpr double kTableEntry = 0.15;
+
+// table_cost: weigh table rebuilds against window lookups (single-job
+// kernels); the multi-job kernel of batches keeps preferring tables, which
+// measured faster there.
+sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> &units, bool table_cost = true)
 {
     struct Best {
         double score = -1;
@@ -237,7 +250,16 @@ sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> 
                         const int64_t n_units = (int64_t)h->I * ((J.W + wc - 1) / wc);
                         // PT clusters exchange boundary slots every swap event:
                         // only when one block cannot hold the unit
-                        const double eff = C == 1 ? 1.0 : (J.kind == SQA_KIND_PT ? 0.05 : 0.9);
+                        double eff = C == 1 ? 1.0 : (J.kind == SQA_KIND_PT ? 0.05 : 0.9);
+                        if (table_cost && J.kind == SQA_KIND_SQA && !wolff) {
+                            // a block's sweep in item units: table lookups cost 1 per
+                            // item plus the per-sweep rebuild of every site's table;
+                            // byte windows cost kWindowItem per item and no rebuild
+                            const double items = (double)J.n * J.zr * wc;
+                            const double cost = J.use_lut ? items + kTableEntry * J.lut_entries
+                                                          : kWindowItem * items;
+                            eff *= items / cost;
+                        }
                         const double busy = (double)std::min<int64_t>(n_units, active) * C * eff;
                         const bool better = busy > best.score * 1.0001 ||
                                             (busy >= best.score * 0.9999 && C == best.C &&
@@ -552,7 +574,7 @@ sqa_status plan_job(sqa_handle *h, int c_forced, int force_wc, JobDev &J, std::v
     const int keep = h->force_wc;
     h->force_wc = force_wc;
     J = h->job;
-    const sqa_status st = plan_shape(h, c_forced, J, units);
+    const sqa_status st = plan_shape(h, c_forced, J, units, false);
     h->force_wc = keep;
     return st;
 }
@@ -819,7 +841,7 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
         // for a single block per unit
         JobDev J = h->job;
         std::vector<Unit> ju;
-        if ((st = plan_shape(h, 1, J, ju)) != SQA_OK) return st;
+        if ((st = plan_shape(h, 1, J, ju, false)) != SQA_OK) return st;
         J.t0 = 0;
         J.t1 = h->S;
         jobs.push_back(J);

@@ -71,8 +71,9 @@ int64_t estimate_device_bytes(const sqa_desc *d);
 void destroy_on_stream(sqa_handle *h, cudaStream_t s);
 // One launch of a job's own sweep kernel over all its units.
 cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s);
-// Plans h's launch (J, units) with c_forced blocks per cluster (0: any) and
-// force_wc words per unit (0: the planner's choice), without changing h.
+// Plans h's launch (J, units) for the multi-job kernel of batches, with
+// c_forced blocks per cluster (0: any) and force_wc words per unit (0: the
+// planner's choice), without changing h.
 sqa_status plan_job(sqa_handle *h, int c_forced, int force_wc, JobDev &J, std::vector<Unit> &units);
 // Sweeps [t0, t1) of every unit of h with its current launch shape, on s.
 sqa_status run_sweeps(sqa_handle *h, int t0, int t1, cudaStream_t s);
