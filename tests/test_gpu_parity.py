@@ -345,6 +345,25 @@ def test_launch_shapes_give_the_oracle_bits(emb, use_table, wc):
         assert np.array_equal(st[i], q.s)
 
 
+def test_planner_weighs_table_rebuilds():
+    """Single-job plans take code tables where a block holds many items per
+    table entry (the 1024 x 256 ME K_8 workload: one block per unit, 8 words)
+    and byte windows where the per-sweep table rebuild would dominate (an
+    8-block cluster of one ME K_21 instance at L = 128); batches keep tables.
+    Planning only: the bits do not depend on the choice (tested above)."""
+    cfg = W.me_n8_batch_config(sweeps=10)
+    h = pkg.Handle(embedding="me", N=8, J=cfg["J"], penalty=cfg["penalty"], sweeps=10, R=256, seed=0, L=64,
+                   beta=cfg["beta"])
+    got = h.launch()
+    h.close()
+    assert (got["use_table"], got["cluster"], got["words_per_unit"]) == (1, 1, 8), got
+    J = W.random_instances(21, 1, 80)
+    h = pkg.Handle(embedding="me", N=21, J=J, penalty=6, sweeps=10, R=175, seed=80, L=128, beta=10 / 3)
+    got = h.launch()
+    h.close()
+    assert got["use_table"] == 0 and got["cluster"] > 1, got
+
+
 @pytest.mark.parametrize("kind,emb,N,Z,R,C", [("sqa", "lhz", 8, 16, 64, 2), ("sqa", "me", 12, 16, 40, 4),
                                               ("sqa", "lhz", 6, 16, 33, 8), ("pt", "me", 8, 8, 64, 2),
                                               ("pt", "lhz", 7, 8, 32, 4), ("pt", "me", 5, 16, 40, 8),
