@@ -345,6 +345,16 @@ def test_launch_shapes_give_the_oracle_bits(emb, use_table, wc):
         assert np.array_equal(st[i], q.s)
 
 
+def test_oversized_unit_is_refused():
+    """One 32-replica word of LHZ K_64 at L = 1024 is 8 MB of state, more than
+    a 16-block cluster's shared memory: the job is refused at planning (no
+    launch), not run from HBM."""
+    J = W.random_instances(64, 1, 3)
+    with pytest.raises(pkg.SQAError) as e:
+        pkg.Handle(embedding="lhz", N=64, J=J, penalty=9, sweeps=2, R=32, seed=3, L=1024, beta=1.0)
+    assert e.value.status == pkg.SQA_ERR_UNSUPPORTED
+
+
 def test_planner_weighs_table_rebuilds():
     """Single-job plans take code tables where a block holds many items per
     table entry (the 1024 x 256 ME K_8 workload: one block per unit, 8 words)
