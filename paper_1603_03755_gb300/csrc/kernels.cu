@@ -17,9 +17,10 @@
 //
 // Per item (site, z, word) the single-spin sweep draws the item's four
 // Philox blocks (16 high uniform bits per replica), forms for each term of
-// the site the word of replicas whose term value is negative (code tables:
-// whose spin product is -1, the table folding in the weight's sign) and, for
-// SQA, the two temporal disagreement words, turns them into one threshold
+// the site the word of replicas whose term value is negative (the
+// two-spin-term table path: whose spin product is -1, its tables folding in
+// the weight's sign) and, for SQA, the two temporal disagreement words,
+// turns them into one threshold
 // index per replica (a per-site code table after an 8x8 bit-matrix
 // transpose, or byte-wise sums into the site's window of the threshold
 // row), and compares
