@@ -5,8 +5,10 @@ single-spin sweep: at a frozen (A, B) it samples
 exp(-alpha sum_tau E_P(sigma^tau) + Jperp sum sigma^tau sigma^{tau+1}),
 enumerated over every path (chi-square), and at large L it approaches the
 quantum single-spin closed form.  The bond probability is pinned to its
-closed form 1 - e^(-2 Jperp) = 1 - tanh(beta A / L); the three random
-streams are pinned as uniform; resume and replica subsets give the same bits.
+closed form 1 - e^(-2 Jperp) = 1 - tanh(beta A / L); at L = 4 and 8 on a
+4-spin problem it matches the exact finite-L transfer-matrix value; the
+three random streams are pinned as uniform; resume and replica subsets give
+the same bits.
 """
 import math
 
@@ -17,7 +19,8 @@ from scipy import stats
 
 import oracle as O
 import workloads as W
-from test_oracle_statistics import _chisq_p, _path_index, _trotter_weights
+from test_oracle_statistics import (_all_states, _chisq_p, _energy_np, _path_index, _thermal_expectation,
+                                    _trotter_expectation, _trotter_weights)
 
 
 def _sample_paths(pb, L, beta, A0, B0, seed, R=128, S=3000, burn=40, every=3):
@@ -82,6 +85,32 @@ def test_wolff_single_spin_quantum_limit():
     w = math.sqrt(A0 ** 2 + (B0 * J[0]) ** 2)
     exact = -(B0 * J[0] / w) * math.tanh(beta * w)
     assert abs(est - exact) < 0.02, (est, exact)
+
+
+def test_wolff_finite_trotter_number_transfer_matrix():
+    """ME of K_2 (4 spins; 32 path bits at L = 8, beyond enumeration) at a
+    frozen (A, B) with a large Trotter error: the cluster move's <H_P> at
+    L = 4 and 8 equals the exact finite-L value from the transfer matrix
+    (exp((beta A / L) sigma^x) per spin), not the other L's nor the limit."""
+    pb = O.Problem("me", 2, np.array([2], np.int32), 1)
+    states, used = _all_states(pb)
+    diagE = _energy_np(pb, states).astype(np.float64)
+    m = len(used)
+    beta, A0, B0 = 3.0, 1.0, 0.6
+    exact = {L: _trotter_expectation(diagE, m, beta, A0, B0, L) for L in (4, 8, 16)}
+    limit = _thermal_expectation(diagE, m, beta, A0, B0)
+    for L in (4, 8):
+        S = 1600
+        q = O.SQA(pb, L, 256, beta, np.full(S, A0), np.full(S, B0), seed=60 + L, move="wolff")
+        q.run(0, 100)
+        acc = []
+        for t in range(100, S, 6):
+            q.run(t, t + 6)
+            acc.append(q.slice_energies().mean())
+        est = float(np.mean(acc))
+        assert abs(est - exact[L]) < 0.03, (L, est, exact[L])
+        others = [exact[k] for k in (4, 8, 16) if k != L] + [limit]
+        assert min(abs(est - o) for o in others) > 0.12, (L, est, others)
 
 
 @pytest.mark.parametrize("beta,A,L", [(10 / 3, 0.9, 64), (10 / 3, 0.01, 64), (1.0, 0.5, 8), (20.0, 1e-4, 128)])
