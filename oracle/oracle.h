@@ -57,50 +57,68 @@ typedef struct {
     const int32_t *inc_term;   /* [inc_ptr[n]] */
 } orc_problem;
 
-/* Minor embedding of K_N on an Lc x Lc Chimera, Lc = ceil(N/4). */
+/* Minor embedding of K_N on an Lc x Lc Chimera, Lc = ceil(N/4) (Sec. II A;
+ * the layout of Fig. 1b, written out in embed.c): grid size, site count,
+ * term count (N(N-1)/2 couplers and N*Lc chain edges) and site index. */
 int32_t orc_me_lc(int32_t N);
 int32_t orc_me_n_sites(int32_t N);
 int32_t orc_me_n_terms(int32_t N);
 int32_t orc_me_site(int32_t Lc, int32_t r, int32_t c, int32_t u, int32_t k);
-/* Writes terms, used, colour; chain_sites [N*(Lc+1)] (logical i's chain at
- * i*(Lc+1)); hub [N].  Returns the number of terms. */
+/* The minor-embedded problem (Sec. II A): couplers J_ij between chains and
+ * chain edges of weight -penalty.  Writes terms, used, colour; chain_sites
+ * [N*(Lc+1)] (logical i's chain at i*(Lc+1)); hub [N].  Returns the number
+ * of terms. */
 int32_t orc_me_build(int32_t N, const int32_t *J, int32_t penalty, int32_t *term_size,
                      int32_t *term_mem, int32_t *term_w, uint8_t *used, int32_t *colour,
                      int32_t *chain_sites, int32_t *hub);
 
-/* LHZ embedding of K_N: K = N(N-1)/2 pair spins, (N-1)(N-2)/2 constraints. */
+/* LHZ embedding of K_N (Sec. II B, Eq. 2): K = N(N-1)/2 pair spins with
+ * local fields J_ij, (N-1)(N-2)/2 constraints -lambda * prod of 3 or 4 pair
+ * spins (Fig. 1c, written out in embed.c): pair index, counts, problem. */
 int32_t orc_lhz_index(int32_t N, int32_t i, int32_t j);
 int32_t orc_lhz_n_sites(int32_t N);
 int32_t orc_lhz_n_terms(int32_t N);
 int32_t orc_lhz_build(int32_t N, const int32_t *J, int32_t lambda, int32_t *term_size,
                       int32_t *term_mem, int32_t *term_w, uint8_t *used, int32_t *colour);
 
-/* Fills inc_ptr [n+1] and inc_term [sum of term sizes]. */
+/* The terms that contain each site (bookkeeping for the energy change of a
+ * flip): fills inc_ptr [n+1] and inc_term [sum of term sizes]. */
 void orc_incidence(int32_t n, int32_t n_terms, const int32_t *term_size,
                    const int32_t *term_mem, int32_t *inc_ptr, int32_t *inc_term);
 
-/* Energy of replica rho of a state stored [n][R]. */
+/* Energy of replica rho of a state stored [n][R]: sum over terms of
+ * w * prod sigma (Eq. 1 through the embedding, Eq. 2 for LHZ). */
 int64_t orc_energy(const orc_problem *pb, const int8_t *s, int32_t R, int32_t rho);
-/* Energy change when sigma_site of replica rho flips. */
+/* Energy change when sigma_site of replica rho flips (the delta of the
+ * Metropolis rule, App. B): minus twice the terms that contain the site. */
 int64_t orc_flip_delta(const orc_problem *pb, const int8_t *s, int32_t R, int32_t rho,
                        int32_t site);
 
-/* ---- acceptance tables ---- */
+/* ---- acceptance tables (Eq. 3, App. B; Eq. 9 for the swaps) ---- */
+/* Coupling along imaginary time of the Trotter action (the paper defers the
+ * action to its references; the standard Suzuki-Trotter form):
+ * Jperp = -1/2 ln tanh(beta A / L), infinite when A = 0. */
 double orc_jperp(double beta, double A, int32_t L);
+/* Exponent of a single-spin flip in that action: x = alpha delta + 2 Jperp m,
+ * alpha = beta B / L, m = sigma (sigma_up + sigma_down); Jperp * 0 = 0. */
 double orc_sqa_x(double alpha, double jperp, int32_t delta, int32_t m);
+/* Metropolis acceptance threshold for exponent x: accept iff x <= 0 or
+ * u < T(x) = min(floor(2^32 exp(-x)), 2^32 - 2). */
 uint32_t orc_threshold(double x);
 /* T[t - t0][(delta - dmin)/2][(m + 2)/2] for even delta in [dmin, dmax]. */
 void orc_sqa_table(const double *A, const double *B, double beta, int32_t L, int32_t t0,
                    int32_t t1, int32_t dmin, int32_t dmax, uint32_t *T);
-/* T[p][(delta - dmin)/2] with x = beta_p * delta. */
+/* PT (App. B): T[p][(delta - dmin)/2] with x = beta_p * delta. */
 void orc_pt_table(const double *betas, int32_t P, int32_t dmin, int32_t dmax, uint32_t *T);
+/* Replica-exchange threshold (Eq. 9): the exponent (beta_p - beta_q) dE of
+ * swapping configurations whose energies differ by dE. */
 uint32_t orc_swap_threshold(double beta_p, double beta_q, int64_t dE);
 
-/* ---- random numbers of the chain ---- */
+/* ---- random numbers of the chain (Philox streams; the paper only asks for
+ * uniform random numbers, so the streams are this implementation's) ---- */
 uint32_t orc_sweep_uniform(uint64_t seed, uint32_t t, uint32_t slot, uint32_t rho, uint32_t inst);
 uint32_t orc_swap_uniform(uint64_t seed, uint32_t event, uint32_t pair, uint32_t rho, uint32_t inst);
 uint32_t orc_tree_draw(uint64_t seed, int32_t inst, int32_t tree, int32_t pos, int32_t N);
-/* Initial spins of a state [Z][n][R]; unused sites are +1. */
 /* Time-like cluster move streams (see anneal.c).  Start slice of replica
  * rho's cluster at site (canonical index), sweep t: floor(u L / 2^32) with u
  * word rho%4 of WSTART at counter (t, site, rho/4, inst).  Bond uniform of the
@@ -112,6 +130,8 @@ uint32_t orc_wolff_start(uint64_t seed, uint32_t t, uint32_t site, uint32_t rho,
 uint32_t orc_wolff_bond_uniform(uint64_t seed, uint32_t t, uint32_t site, int32_t L, int32_t tau, uint32_t rho,
                                 uint32_t inst);
 uint32_t orc_wolff_accept_uniform(uint64_t seed, uint32_t t, uint32_t site, uint32_t rho, uint32_t inst);
+/* Initial spins of a state [Z][n][R], iid uniform from the INIT stream (the
+ * paper does not state the initial state); unused sites are +1. */
 void orc_init_spins(const orc_problem *pb, int32_t Z, int32_t R, uint64_t seed, int32_t inst,
                     int8_t *s);
 
@@ -125,14 +145,16 @@ typedef struct {
     const double *B;    /* [S] problem schedule */
     uint64_t seed;
 } orc_sqa_params;
+/* SQA (Eq. 3, App. B, Sec. III): at sweep t, every spin of every slice by
+ * colour class with single-spin Metropolis in the Trotter action above. */
 int32_t orc_sqa_run(const orc_problem *pb, const orc_sqa_params *prm, int8_t *s, int32_t inst,
                     int32_t t0, int32_t t1, int32_t rho0, int32_t rho1);
 /* Probability threshold of joining two equal neighbouring slices into one
- * time-like cluster: p = 1 - e^(-2 Jperp) = 1 - tanh(beta A / L);
+ * time-like cluster (Sec. III, Sec. V): p = 1 - e^(-2 Jperp) = 1 - tanh(beta A / L);
  * 0xFFFFFFFF (always) when A <= 0, else min(floor(2^32 p), 2^32 - 2). */
 uint32_t orc_bond_threshold(double beta, double A, int32_t L);
-/* The same anneal with one time-like cluster move per (site, replica) per
- * sweep instead of the single-spin sweep. */
+/* The same anneal with one time-like (Wolff) cluster move per (site,
+ * replica) per sweep instead of the single-spin sweep (Sec. III, Sec. V). */
 int32_t orc_sqa_wolff_run(const orc_problem *pb, const orc_sqa_params *prm, int8_t *s, int32_t inst,
                           int32_t t0, int32_t t1, int32_t rho0, int32_t rho1);
 
@@ -144,15 +166,24 @@ typedef struct {
     const double *betas;  /* [P], strictly decreasing (coldest first) */
     uint64_t seed;
 } orc_pt_params;
+/* Zero-field parallel tempering (App. B, Eq. 9): single-spin Metropolis
+ * sweeps at each slot's beta, replica-exchange swaps of neighbouring slots
+ * every swap_every sweeps (even and odd pairs in turn). */
 int32_t orc_pt_run(const orc_problem *pb, const orc_pt_params *prm, int8_t *s, int64_t *E,
                    int32_t inst, int32_t t0, int32_t t1, int32_t rho0, int32_t rho1);
 
 /* ---- decoding (readout of one replica: phys[n] = sigma) ---- */
+/* ME majority vote over each chain (Eq. 4); ties take the chain's hub spin. */
 void orc_me_decode(int32_t N, const int32_t *chain_sites, const int32_t *hub,
                    const int8_t *phys, int8_t *logical);
+/* Spanning trees of the logical graph for LHZ decoding (App. A): random
+ * uniform labelled trees (Pruefer sequences from the TREE stream), the star
+ * (Eq. 10) and the chain (Eq. 11). */
 void orc_prufer_tree(int32_t N, uint64_t seed, int32_t inst, int32_t tree, int32_t *parent);
 void orc_star_tree(int32_t N, int32_t *parent);
 void orc_chain_tree(int32_t N, int32_t *parent);
+/* LHZ decoding along one tree (App. A): q_0 = +1, a child is its parent times
+ * the pair spin between them. */
 void orc_lhz_tree_decode(int32_t N, const int32_t *parent, const int8_t *phys, int8_t *logical);
 /* Minimum-weight decoding of an LHZ readout (Sec. IV A): the logical state
  * whose pair products q_i q_j disagree with the fewest pair spins of phys,
@@ -168,9 +199,13 @@ void orc_lhz_mwd_decode(int32_t N, const int8_t *phys, int8_t *logical);
  * logical state from p (q_0 = +1). */
 void orc_lhz_bp_decode(int32_t N, const int8_t *phys, double error_rate, int32_t iterations, const int32_t *parent,
                        int8_t *logical);
+/* Majority vote over n_trees tree decodings (Eq. 5); ties take the first. */
 void orc_lhz_vote_decode(int32_t N, int32_t n_trees, const int32_t *parents,
                          const int8_t *phys, int8_t *logical);
+/* Logical energy sum_{i<j} J_ij s_i s_j (Eq. 1, h = 0). */
 int64_t orc_logical_energy(int32_t N, const int32_t *J, const int8_t *s);
+/* Exact logical ground-state energy by enumeration of the 2^(N-1) states
+ * with s_{N-1} = +1 (success is reaching it, Sec. III). */
 int64_t orc_ground_energy(int32_t N, const int32_t *J, int8_t *s_best);
 
 #ifdef __cplusplus
