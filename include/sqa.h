@@ -126,7 +126,10 @@ typedef struct {
  * device state; draws the initial spins.  Synchronous.  On error *out is
  * NULL. */
 sqa_status sqa_create(const sqa_desc *desc, sqa_handle **out);
+/* Waits for the device, then frees everything the handle holds (a library
+ * service, as are the info, tuning and error calls).  NULL is a no-op. */
 void sqa_destroy(sqa_handle *h);
+/* Sizes of a created handle into *out (caller-owned). */
 sqa_status sqa_get_info(const sqa_handle *h, sqa_info *out);
 
 /* Launch shape of the sweep kernel (the autotuner's knobs; results do not
@@ -143,13 +146,16 @@ sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t 
                           int32_t *smem_bytes, int32_t *cluster);
 
 /* Runs the whole program: fresh initial spins, then sweeps 0..S-1 (SQA
- * anneal, or PT with swaps every swap_every sweeps), as one persistent
- * launch over all instances.  Asynchronous on stream. */
+ * anneal: Metropolis on the Trotterised H(t) of Eq. 3, App. B, Sec. III; or
+ * PT with swaps every swap_every sweeps: App. B, Eq. 9), as one persistent
+ * launch over all instances.  Asynchronous on stream; a launch error is
+ * returned as SQA_ERR_CUDA. */
 sqa_status sqa_run(sqa_handle *h, void *stream);
 
-/* Sweeps t0..t1-1 continuing from the current state (t0 == 0 draws fresh
- * initial spins first).  Runs split at any t give the same bits as one run
- * (checkpoint/resume). */
+/* Sweeps t0..t1-1 of the same program (Eq. 3, App. B) continuing from the
+ * current state (t0 == 0 draws fresh initial spins first).  Runs split at
+ * any t give the same bits as one run (checkpoint/resume).  t outside
+ * 0 <= t0 <= t1 <= S -> SQA_ERR_INVALID. */
 sqa_status sqa_run_sweeps(sqa_handle *h, int32_t t0, int32_t t1, void *stream);
 
 /* The plain path kept for comparison: the same sweeps as sqa_run, but one
@@ -167,14 +173,19 @@ sqa_status pt_run(sqa_handle *h, const double *betas, int32_t n_temps, int32_t n
                   int32_t swap_every, void *stream);
 
 /* One persistent launch over the units of several handles of any shapes
- * (ragged batching); each handle runs its whole program as in sqa_run. */
+ * (ragged batching); each handle runs its whole program as in sqa_run
+ * (Eq. 3 / App. B, Eq. 9), with the same bits.  hs: n caller-owned handles. */
 sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream);
 
-/* Readout: slice 0 (SQA) or the coldest slot (PT); out [I][n_phys][W]. */
+/* Readout of the final state (App. B: one Trotter slice, here slice 0; PT:
+ * the coldest slot): out [I][n_phys][W] uint32, bit b of word w = replica
+ * 32w + b, 1 <-> sigma = -1, canonical site order; out is caller-owned,
+ * host (synchronous) or device (out_is_device, asynchronous on stream). */
 sqa_status sqa_readout(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *stream);
-/* Whole state; out [I][Z][n_phys][W]. */
+/* Whole state, every slice or slot; out [I][Z][n_phys][W] as sqa_readout. */
 sqa_status sqa_state(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *stream);
-/* Physical energy E_P of every slice/slot and replica; out [I][Z][R]. */
+/* Physical energy E_P (Eq. 1 through the embedding; Eq. 2 for LHZ) of every
+ * slice/slot and replica; out [I][Z][R] int32, as sqa_readout. */
 sqa_status sqa_energies(sqa_handle *h, int32_t *out, int32_t out_is_device, void *stream);
 
 /* Decodes the readout of every replica to a logical state and its logical
@@ -188,9 +199,10 @@ sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *lo
                       int64_t *energy_out, const int64_t *e_ground, int32_t *success_out,
                       int32_t out_is_device, void *stream);
 
-/* Exact logical ground-state energies by exhaustive search over the 2^(N-1)
- * states with s_{N-1} = +1 (h = 0), on the GPU.  J host [I][N(N-1)/2];
- * e_out host [I].  N <= 40.  Synchronous. */
+/* Exact logical ground-state energies of Eq. 1 (h = 0; success means
+ * reaching it, Sec. III) by exhaustive search over the 2^(N-1) states with
+ * s_{N-1} = +1, on the GPU.  J host [I][N(N-1)/2]; e_out host [I].  N <= 40.
+ * Synchronous. */
 sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, int64_t *e_out);
 
 /* Exhaustive ground-state energies for callers that cannot allocate device
@@ -223,7 +235,11 @@ sqa_status sqa_decode_bp(sqa_handle *h, double error_rate, int32_t iterations, i
 /* ---- reusable batches (CUDA graph) and the launch-shape autotuner ---- */
 
 typedef struct sqa_batch sqa_batch;
-/* Plans the handles (SQA or PT, any sizes) once for one persistent launch of
+/* Batches, the autotuner and the server are library services: the paper's
+ * instances and runs are independent jobs, and these only schedule them
+ * (each job's results are those of sqa_run).
+ *
+ * Plans the handles (SQA or PT, any sizes) once for one persistent launch of
  * the multi-job sweep kernel: every job's units in one list, longest first.
  * The handles must outlive the batch and must not be tuned, switched to PT
  * (pt_run) or destroyed while it exists. */
@@ -313,14 +329,14 @@ sqa_status sqa_plan_terms(int32_t embedding, int32_t N, const int32_t *J, int32_
  * 32-replica word, so an upper bound.  Host only; 0 on an invalid desc. */
 int64_t sqa_plan_device_bytes(const sqa_desc *desc);
 
-/* The acceptance thresholds sqa_create would upload for desc: SQA
+/* The acceptance thresholds (Eq. 3, App. B) sqa_create would upload for desc: SQA
  * [S][nd][3] indexed by ((delta - dmin)/2, (m + 2)/2), PT [P][nd] indexed
  * by (delta - dmin)/2, nd = (dmax - dmin)/2 + 1.  cap is the length of T. */
 sqa_status sqa_plan_tables(const sqa_desc *desc, uint32_t *T, int64_t cap, int32_t *dmin,
                            int32_t *dmax);
 
-/* The cluster-move tables sqa_create would upload for an SQA desc with
- * move = SQA_MOVE_WOLFF: Tb [S] bond thresholds; acc_off, acc_len [S] and
+/* The cluster-move tables (Sec. III, Sec. V) sqa_create would upload for an
+ * SQA desc with move = SQA_MOVE_WOLFF: Tb [S] bond thresholds; acc_off, acc_len [S] and
  * Tacc (cap entries) the acceptance thresholds T(alpha_t D) of sweep t for
  * D = 2, 4, ..., 2 acc_len[t] at Tacc[acc_off[t] + D/2 - 1]; *n_acc gets the
  * total.  Any output may be NULL to query sizes. */
@@ -332,11 +348,12 @@ sqa_status sqa_plan_wolff_tables(const sqa_desc *desc, uint32_t *Tb, int32_t *ac
 sqa_status sqa_plan_swap_table(const double *betas, int32_t n_temps, int32_t pair, uint32_t *out,
                                int32_t cap, int32_t *len);
 
-/* The random spanning tree number `tree` of instance `inst` used by
- * SQA_DECODE_LHZ_TREES: parent[v], parent[0] = -1. */
+/* The random spanning tree (App. A) number `tree` of instance `inst` used
+ * by SQA_DECODE_LHZ_TREES: parent[v], parent[0] = -1. */
 sqa_status sqa_plan_tree(int32_t N, uint64_t seed, int32_t inst, int32_t tree, int32_t *parent);
 
-/* Diagnostic: sustained integer instructions per SM clock (all lanes) of one
+/* Diagnostic for the roofline (no paper counterpart): sustained integer
+ * instructions per SM clock (all lanes) of one
  * instruction kind on the current device, from a dependency-free
  * microbenchmark timed with the SM clock counter.  kind: 0 LOP3, 1 IADD3,
  * 2 IMAD, 3 IMAD.WIDE, 4 IMAD.HI, 5 LOP3/IMAD alternating, 6 Philox4x32-10
