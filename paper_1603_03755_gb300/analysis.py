@@ -82,17 +82,28 @@ def embed_logical(embedding: str, N: int, q) -> np.ndarray:
 def logical_ground_states(N: int, J) -> tuple[int, np.ndarray]:
     """Minimum of sum_{i<j} J_ij q_i q_j (Eq. 1, h = 0) and every logical
     state reaching it, both Z2 partners, [n_ground, N] in the order of the
-    enumeration (q_{N-1} = +1 halves first, then their negations)."""
+    enumeration (q_{N-1} = +1 halves first, then their negations).  The
+    2^(N-1) states are enumerated in chunks; N <= 26."""
+    if not 2 <= N <= 26:
+        raise ValueError("exhaustive enumeration needs 2 <= N <= 26")
     J = np.asarray(J, np.int64)
-    x = np.arange(1 << (N - 1), dtype=np.int64)
-    Q = np.ones((x.size, N), np.int64)
-    for i in range(N - 1):
-        Q[:, i] = np.where((x >> i) & 1, -1, 1)
-    E = np.zeros(x.size, np.int64)
-    for k, (i, j) in enumerate(_pairs(N)):
-        E += J[k] * Q[:, i] * Q[:, j]
-    e_min = int(E.min())
-    G = Q[E == e_min]
+    pairs = _pairs(N)
+    e_min, found = None, []
+    chunk = 1 << 16
+    for x0 in range(0, 1 << (N - 1), chunk):
+        x = np.arange(x0, min(x0 + chunk, 1 << (N - 1)), dtype=np.int64)
+        Q = np.ones((x.size, N), np.int64)
+        for i in range(N - 1):
+            Q[:, i] = np.where((x >> i) & 1, -1, 1)
+        E = np.zeros(x.size, np.int64)
+        for k, (i, j) in enumerate(pairs):
+            E += J[k] * Q[:, i] * Q[:, j]
+        m = int(E.min())
+        if e_min is None or m < e_min:
+            e_min, found = m, [Q[E == m]]
+        elif m == e_min:
+            found.append(Q[E == m])
+    G = np.concatenate(found)
     return e_min, np.concatenate([G, -G]).astype(np.int8)
 
 
