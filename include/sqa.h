@@ -202,7 +202,9 @@ sqa_status sqa_decode(sqa_handle *h, int32_t method, int32_t n_trees, int8_t *lo
 /* Exact logical ground-state energies of Eq. 1 (h = 0; success means
  * reaching it, Sec. III) by exhaustive search over the 2^(N-1) states with
  * s_{N-1} = +1, on the GPU.  J host [I][N(N-1)/2]; e_out host [I].  N <= 40.
- * Synchronous. */
+ * One call enumerates at most 2^40 states in all: I * 2^(N-1) > 2^40 (e.g.
+ * N = 40 with I > 2, N = 32 with I > 512) -> SQA_ERR_UNSUPPORTED, so that no
+ * call holds the device for more than a few seconds.  Synchronous. */
 sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, int64_t *e_out);
 
 /* Exhaustive ground-state energies for callers that cannot allocate device
@@ -214,10 +216,18 @@ sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, i
  * asynchronous on stream, and nothing is allocated: the per-instance running
  * minima live in a fixed device array of 4096 entries (32 KiB held on every
  * device that loads the library, until exit).  I > 4096 or N outside 2..40
- * -> SQA_ERR_INVALID.  The first call on a device looks up that array's
- * address (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  All calls share the array and reset it at the start,
- * so calls that overlap on the GPU race with each other. */
+ * -> SQA_ERR_INVALID; I * 2^(N-1) > 2^40 -> SQA_ERR_UNSUPPORTED (the same
+ * work bound as sqa_ground_energy).  J_dev and e_dev must be device (or
+ * managed) memory of the current device, checked with
+ * cudaPointerGetAttributes (SQA_ERR_INVALID otherwise); their lengths cannot
+ * be checked from raw pointers and are the caller's to get right.  The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress) and
+ * caches it with the current CUDA context; a call that finds another context
+ * current (after cudaDeviceReset, say) looks it up again.  Make the first
+ * call on a device, and the first after a reset, before any stream capture.
+ * All calls share the array and reset it at the start, so calls that overlap
+ * on the GPU race with each other; calls queued one after another on one
+ * stream do not. */
 sqa_status sqa_ground_energy_noalloc(int32_t N, int32_t n_instances, const int32_t *J_dev,
                                      int64_t *e_dev, void *stream);
 

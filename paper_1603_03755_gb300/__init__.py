@@ -435,7 +435,19 @@ def int_peak(kind: str) -> float:
 def ground_energy_noalloc(N: int, J_dev, e_dev, stream=None):
     """Allocation-free ground-state search: J_dev [I, N(N-1)/2] int32 and
     e_dev [I] int64 are caller-owned CUDA tensors; asynchronous on stream."""
-    assert J_dev.is_cuda and e_dev.is_cuda and J_dev.is_contiguous() and e_dev.is_contiguous()
+    import torch
+
+    I = e_dev.shape[0] if e_dev.dim() == 1 else -1
+    if not (J_dev.is_cuda and e_dev.is_cuda and J_dev.is_contiguous() and e_dev.is_contiguous()):
+        raise ValueError("ground_energy_noalloc: J_dev and e_dev must be contiguous CUDA tensors")
+    if J_dev.dtype != torch.int32 or e_dev.dtype != torch.int64:
+        raise ValueError("ground_energy_noalloc: J_dev must be int32 and e_dev int64")
+    if I < 1 or tuple(J_dev.shape) != (I, N * (N - 1) // 2):
+        raise ValueError(f"ground_energy_noalloc: J_dev must be [I, N(N-1)/2] and e_dev [I], "
+                         f"got {tuple(J_dev.shape)} and {tuple(e_dev.shape)}")
+    cur = torch.cuda.current_device()
+    if J_dev.device.index != cur or e_dev.device.index != cur:
+        raise ValueError("ground_energy_noalloc: J_dev and e_dev must be on the current CUDA device")
     _check(lib().sqa_ground_energy_noalloc(N, e_dev.shape[0], J_dev.data_ptr(), e_dev.data_ptr(),
                                            _stream_ptr(stream)), "sqa_ground_energy_noalloc")
 

@@ -1,6 +1,8 @@
 // C ABI of the SQA / PT library (include/sqa.h): handle lifecycle, launch
 // planning and the host side of every entry point.
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <math.h>
 #include <string.h>
 
@@ -1072,6 +1074,11 @@ static sqa_status decode_impl(sqa_handle *h, int32_t method, int32_t n_trees, do
 sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, int64_t *e_out)
 {
     if (N < 2 || N > 40 || n_instances < 1 || !J || !e_out) return set_error("ground arguments"), SQA_ERR_INVALID;
+    // a bound on the search's work: one call enumerates at most 2^40 states
+    // in all (a few seconds), so no call can hold the device for hours
+    if ((double)n_instances * std::ldexp(1.0, N - 1) > std::ldexp(1.0, 40))
+        return set_error("sqa_ground_energy: n_instances * 2^(N-1) exceeds the search budget of 2^40 states"),
+               SQA_ERR_UNSUPPORTED;
     sqa_status st = device_ready();
     if (st != SQA_OK) return st;
     const size_t npair = (size_t)N * (N - 1) / 2;
