@@ -15,10 +15,11 @@
  *     w * prod(sigma over its 1..4 members) to the energy;
  *   - Philox4x32-10 keys (seed_lo, seed_hi ^ domain) with the domain words
  *     below;
- *   - the per-attempt uniform u is 32 bits: its high 16 bits come from the
- *     SWEEP_HI stream and its low 16 bits from the SWEEP_LO stream, both at
- *     counter (t, site*Z + z, rho/8, instance), half (rho%8)&1 of output word
- *     (rho%8)/2 (half 0 = bits 0..15);
+ *   - the per-attempt uniform u is 32 bits, u = h * 2^25 + l: h (7 bits) is
+ *     the low 7 bits of byte (r/8) of output word (r%4) of the SWEEP_HI
+ *     stream at counter (t, site*Z + z, 2*(rho/32) + (r/4)%2, instance),
+ *     r = rho%32; l (25 bits) is output word (rho%4) of the SWEEP_LO stream
+ *     at counter (t, site*Z + z, rho/4, instance), shifted right by 7;
  *   - acceptance: accept iff x <= 0 or u < T(x), with
  *     T(x) = min(floor(2^32 exp(-x)), 2^32 - 2) for x > 0.
  */

@@ -46,22 +46,26 @@ static void stream_key(uint64_t seed, uint32_t domain, uint32_t key[2])
     key[1] = (uint32_t)(seed >> 32) ^ domain;
 }
 
-/* The 16-bit half of output word (j/2), half (j&1), for replica slot j = rho % 8. */
-static uint32_t half16(const uint32_t out[4], uint32_t j)
-{
-    return (out[j >> 1] >> (16u * (j & 1u))) & 0xFFFFu;
-}
-
+/* The per-attempt uniform of the single-spin sweep (SQA and PT), u = h * 2^25 + l:
+ *   h, its 7 high bits: the low 7 bits of byte (r / 8) of output word (r % 4)
+ *     of the SWEEP_HI block at counter (t, slot, 2 * (rho / 32) + (r / 4) % 2, inst),
+ *     r = rho % 32 (one block serves 16 replicas of a 32-replica word);
+ *   l, its 25 low bits: output word (rho % 4) of the SWEEP_LO block at counter
+ *     (t, slot, rho / 4, inst), shifted right by 7.
+ * Both are independent uniform bit strings, so u is uniform on [0, 2^32). */
 uint32_t orc_sweep_uniform(uint64_t seed, uint32_t t, uint32_t slot, uint32_t rho, uint32_t inst)
 {
-    uint32_t ctr[4] = {t, slot, rho >> 3, inst};
+    uint32_t r = rho & 31u;
     uint32_t khi[2], klo[2], a[4], b[4];
     stream_key(seed, ORC_DOM_SWEEP_HI, khi);
     stream_key(seed, ORC_DOM_SWEEP_LO, klo);
-    orc_philox4x32_10(ctr, khi, a);
-    orc_philox4x32_10(ctr, klo, b);
-    uint32_t j = rho & 7u;
-    return (half16(a, j) << 16) | half16(b, j);
+    uint32_t ca[4] = {t, slot, 2u * (rho >> 5) + ((r >> 2) & 1u), inst};
+    uint32_t cb[4] = {t, slot, rho >> 2, inst};
+    orc_philox4x32_10(ca, khi, a);
+    orc_philox4x32_10(cb, klo, b);
+    uint32_t h = (a[r & 3u] >> (8u * (r >> 3))) & 0x7Fu;
+    uint32_t l = b[rho & 3u] >> 7;
+    return (h << 25) | l;
 }
 
 uint32_t orc_swap_uniform(uint64_t seed, uint32_t event, uint32_t pair, uint32_t rho, uint32_t inst)

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "layout.cuh"
 
 using namespace sqa;
 
@@ -38,7 +39,8 @@ struct sqa_batch {
     JobDev *d_jobs = nullptr;
     Unit *d_units = nullptr;
     int *d_counter = nullptr;
-    size_t cap_jobs = 0, cap_units = 0;
+    uint2 *d_tieq = nullptr;  // tie queue of the persistent blocks (JobDev::tieq)
+    size_t cap_jobs = 0, cap_units = 0, cap_tieq = 0;
     cudaGraphExec_t exec = nullptr;
 };
 
@@ -95,6 +97,21 @@ sqa_status plan_batch(sqa_batch *b, int trial)
         b->cap_units = b->units.size();
     }
     b->grid = grid_for((const void *)sweep_kernel, b->smem, (int)b->units.size());
+    // one tie queue for the persistent blocks: the largest phase of any job
+    int stride = 1;
+    for (const JobDev &J : b->jobs) stride = std::max(stride, tie_items(J, J.wc));
+    const size_t need = (size_t)b->grid * (size_t)stride;
+    if (need > b->cap_tieq) {
+        if (b->d_tieq) cudaFree(b->d_tieq);
+        b->d_tieq = nullptr;
+        b->cap_tieq = 0;
+        SQA_TRY(cudaMalloc((void **)&b->d_tieq, need * sizeof(uint2)));
+        b->cap_tieq = need;
+    }
+    for (JobDev &J : b->jobs) {
+        J.tieq = b->d_tieq;
+        J.tieq_stride = stride;
+    }
     SQA_TRY(cudaMemcpy(b->d_jobs, b->jobs.data(), b->jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice));
     SQA_TRY(cudaMemcpy(b->d_units, b->units.data(), b->units.size() * sizeof(Unit), cudaMemcpyHostToDevice));
     drop_graph(b);
@@ -252,6 +269,7 @@ void sqa_batch_destroy(sqa_batch *b)
     if (b->d_jobs) cudaFree(b->d_jobs);
     if (b->d_units) cudaFree(b->d_units);
     if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_tieq) cudaFree(b->d_tieq);
     delete b;
 }
 

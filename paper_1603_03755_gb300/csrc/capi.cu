@@ -156,6 +156,8 @@ void free_all(sqa_handle *h, cudaStream_t s = 0)
     h->d_units = nullptr;
     h->n_units = 0;
     h->d_counter = nullptr;
+    h->d_tieq = nullptr;
+    h->tieq_cap = 0;
 }
 
 
@@ -290,6 +292,28 @@ sqa_status plan_shape(sqa_handle *h, int c_forced, JobDev &J, std::vector<Unit> 
 
 sqa_status plan_units(sqa_handle *h) { return plan_shape(h, h->force_cluster, h->job, h->units); }
 
+// Entries of a job's tie queue: every item of one colour phase of every
+// unit, for any launch shape (grid x items per block phase <= units x words x
+// phase items per word, and words per unit round the W words up to at most
+// 2W).  Host-only, so the admission estimate is exact.
+int64_t tieq_entries(const Plan &pl, int kind, int move, int64_t I, int64_t Z, int64_t W)
+{
+    if (kind == SQA_KIND_SQA && move == SQA_MOVE_WOLFF) return 0;
+    int nq = 0;
+    for (int c = 0; c < pl.ncol; c++) nq = std::max(nq, pl.col_ptr[c + 1] - pl.col_ptr[c]);
+    const int64_t zn = kind == SQA_KIND_SQA ? (Z + 1) / 2 : Z;
+    return (int64_t)nq * zn * I * 2 * W;
+}
+
+// Points the job at the handle's tie queue with the current shape's stride
+// (allocated once at setup: tieq_entries covers every shape).
+void set_tieq(sqa_handle *h)
+{
+    JobDev &J = h->job;
+    J.tieq = h->d_tieq;
+    J.tieq_stride = h->d_tieq ? tie_items(J, J.wc) : 0;
+}
+
 sqa_status validate(const sqa_desc *d)
 {
     if (!d) return set_error("desc is NULL"), SQA_ERR_INVALID;
@@ -383,6 +407,11 @@ sqa_status setup_program(sqa_handle *h)
     J.key_hi = shi ^ kDomSweepHi;
     J.key_lo = shi ^ kDomSweepLo;
     J.key_swap = shi ^ kDomSwap;
+    for (int r = 0; r < 10; r++) {
+        J.rk0[r] = J.seed_lo + (uint32_t)r * 0x9E3779B9u;
+        J.rk_hi[r] = J.key_hi + (uint32_t)r * 0xBB67AE85u;
+        J.rk_lo[r] = J.key_lo + (uint32_t)r * 0xBB67AE85u;
+    }
     J.move = wolff ? SQA_MOVE_WOLFF : SQA_MOVE_METROPOLIS;
     J.pairs = 1;
     for (const PlanTerm &t : pl.terms) J.pairs = J.pairs && t.size == 2;
@@ -460,6 +489,12 @@ sqa_status setup_program(sqa_handle *h)
     J.acc_off = h->d_accoff;
     J.acc_len = h->d_acclen;
     if ((st = plan_units(h)) != SQA_OK) return st;
+    {
+        const int64_t ne = tieq_entries(h->plan, h->kind, h->move, h->I, h->job.Z, h->job.W);
+        if (ne > 0 && (st = dalloc(h, &h->d_tieq, (size_t)ne)) != SQA_OK) return st;
+        h->tieq_cap = (size_t)ne;
+        set_tieq(h);
+    }
     if ((st = dalloc(h, &h->d_job, 1)) != SQA_OK) return st;
     if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) return st;
     h->n_units = (int)h->units.size();
@@ -475,11 +510,7 @@ sqa_status launch_sweeps(sqa_handle *h, int t0, int t1, int u0, int nu, cudaStre
     h->job.t0 = t0;
     h->job.t1 = t1;
     SQA_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), s));
-    int grid;
-    if (h->job.csize == 1)
-        grid = grid_for(one_kernel(h->job), h->job.smem_bytes, nu, sweep_one_threads(h->job));
-    else
-        grid = std::max(1, std::min(nu, max_active_clusters(h->job))) * h->job.csize;
+    const int grid = launch_grid(h->job, nu);
     SQA_CUDA(launch_sweep_one(h->job, h->d_units + u0, nu, h->d_counter, grid, s));
     return SQA_OK;
 }
@@ -527,6 +558,12 @@ int grid_for(const void *kernel, int smem_bytes, int n_units, int threads)
     return std::max(1, std::min(n_units, per_sm * g_num_sms));
 }
 
+int launch_grid(const JobDev &J, int n_units)
+{
+    if (J.csize == 1) return grid_for(sweep_one_entry(J), J.smem_bytes, n_units, sweep_one_threads(J));
+    return std::max(1, std::min(n_units, max_active_clusters(J))) * J.csize;
+}
+
 int64_t estimate_device_bytes(const sqa_desc *d)
 {
     if (validate(d) != SQA_OK) return 0;
@@ -568,6 +605,8 @@ int64_t estimate_device_bytes(const sqa_desc *d)
     b += al((int64_t)pl.canon.size() * 4) + al((int64_t)pl.compact.size() * 4) + al((int64_t)I * npair * 4);
     b += d->embedding == SQA_EMB_ME_CHIMERA ? al((int64_t)pl.chain.size() * 4) : al((int64_t)pl.pair.size() * 4);
     b += al((int64_t)sizeof(JobDev)) + al((int64_t)I * W * (int64_t)sizeof(Unit)) + al(4);
+    const int64_t ne = tieq_entries(pl, d->kind, d->move, I, Z, W);
+    if (ne > 0) b += ne * (int64_t)sizeof(uint2);
     return b;
 }
 
@@ -588,12 +627,7 @@ sqa_status run_sweeps(sqa_handle *h, int t0, int t1, cudaStream_t s)
 
 cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s)
 {
-    int grid;
-    if (J.csize == 1)
-        grid = grid_for(sweep_one_entry(J), J.smem_bytes, n_units, sweep_one_threads(J));
-    else
-        grid = std::max(1, std::min(n_units, max_active_clusters(J))) * J.csize;
-    return launch_sweep_one(J, units, n_units, counter, grid, s);
+    return launch_sweep_one(J, units, n_units, counter, launch_grid(J, n_units), s);
 }
 
 }  // namespace sqa
@@ -757,6 +791,7 @@ sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, in
         return st;
     }
     h->n_units = (int)h->units.size();
+    set_tieq(h);
     return SQA_OK;
 }
 
@@ -863,7 +898,16 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
     JobDev *d_jobs = nullptr;
     Unit *d_units = nullptr;
     int *d_counter = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(JobDev), s);
+    uint2 *d_tieq = nullptr;
+    const int grid = grid_for((const void *)sweep_kernel, smem, (int)units.size());
+    int stride = 1;
+    for (const JobDev &J : jobs) stride = std::max(stride, tie_items(J, J.wc));
+    cudaError_t e = cudaMallocAsync((void **)&d_tieq, (size_t)grid * stride * sizeof(uint2), s);
+    for (JobDev &J : jobs) {
+        J.tieq = d_tieq;
+        J.tieq_stride = stride;
+    }
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(JobDev), s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_units, units.size() * sizeof(Unit), s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_counter, sizeof(int), s);
     if (e == cudaSuccess)
@@ -872,12 +916,12 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
         e = cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
     if (e == cudaSuccess) {
-        const int grid = grid_for((const void *)sweep_kernel, smem, (int)units.size());
         sweep_kernel<<<grid, kThreads, smem, s>>>(d_jobs, d_units, (int)units.size(), d_counter);
         e = cudaGetLastError();
     }
     // freed in stream order after the launch (or at once on an error); host
     // vectors are consumed: pageable copies are staged before return
+    if (d_tieq) cudaFreeAsync(d_tieq, s);
     if (d_jobs) cudaFreeAsync(d_jobs, s);
     if (d_units) cudaFreeAsync(d_units, s);
     if (d_counter) cudaFreeAsync(d_counter, s);

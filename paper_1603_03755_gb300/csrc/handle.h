@@ -40,6 +40,8 @@ struct sqa_handle {
     sqa::Unit *d_units = nullptr;
     int n_units = 0;
     int *d_counter = nullptr;
+    uint2 *d_tieq = nullptr;  // tie queue of the single-spin sweep (JobDev::tieq)
+    size_t tieq_cap = 0;      // its entries
     std::vector<sqa::Unit> units;
     int64_t device_bytes = 0;
     int64_t h2d_bytes = 0;
@@ -69,6 +71,8 @@ __global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units,
 int64_t estimate_device_bytes(const sqa_desc *d);
 // Frees h in stream order on s, without a device-wide synchronization.
 void destroy_on_stream(sqa_handle *h, cudaStream_t s);
+// Blocks of a launch of a job's own sweep kernel over n_units units.
+int launch_grid(const JobDev &J, int n_units);
 // One launch of a job's own sweep kernel over all its units.
 cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s);
 // Plans h's launch (J, units) for the multi-job kernel of batches, with

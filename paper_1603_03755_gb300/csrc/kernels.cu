@@ -85,12 +85,17 @@ namespace cg = cooperative_groups;
 struct Smem {
     uint32_t *S;      // [zr][zstride]
     uint32_t *T;      // full thresholds: SQA one row, PT zr rows
-    int32_t *Tq;      // T & 0xFFFF0000: PT zr rows, SQA window mode one row
-    int32_t *lut;     // SQA table mode: per-site tables by code
+    uint8_t *Tb;      // T >> 25: PT zr rows, SQA window mode one row
+    uint32_t lut;     // SQA table mode: shared address of the per-site byte tables (256-byte aligned)
     SiteRec *sites;   // [n]
     int32_t *E;       // PT: [zr][wc*32]
     uint32_t *M;      // PT: swap masks [zr/2+1][wc]
+    uint32_t *qn;     // tie queue counters (two, used by alternate phases)
+    uint32_t *qdiv;   // per colour: the task decode's divisor {m, sh} (FastDiv)
+    uint2 *q;         // this block's tie queue entries {state word, tie mask} (global memory)
 };
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ Smem carve(const JobDev &J, unsigned char *base)
 {
@@ -98,11 +103,14 @@ __device__ __forceinline__ Smem carve(const JobDev &J, unsigned char *base)
     Smem m;
     m.S = (uint32_t *)(base + o.S);
     m.T = (uint32_t *)(base + o.T);
-    m.Tq = (int32_t *)(base + o.Tq);
-    m.lut = (int32_t *)(base + o.lut);
+    m.Tb = (uint8_t *)(base + o.Tb);
+    m.lut = (saddr(base + o.lut) + (kLutSlot - 1)) & ~(uint32_t)(kLutSlot - 1);
     m.sites = (SiteRec *)(base + o.sites);
     m.E = (int32_t *)(base + o.E);
     m.M = (uint32_t *)(base + o.M);
+    m.qn = (uint32_t *)(base + o.Q);
+    m.qdiv = (uint32_t *)(base + o.Q + 16);
+    m.q = J.tieq + (size_t)blockIdx.x * (size_t)J.tieq_stride;
     return m;
 }
 
@@ -122,30 +130,64 @@ __device__ __forceinline__ void cluster_barrier(int C)
         __syncthreads();
 }
 
-// High half of a threshold in place: for a word x whose top 16 bits are a
-// uniform's high half h (any low bits), x >= q iff h >= T >> 16 (reject, but
-// for ties), and x - q lies in [0, 2^16) iff h == T >> 16 (a tie).
-__device__ __forceinline__ int32_t high_part(uint32_t T) { return (int32_t)(T & 0xFFFF0000u); }
+// Division by a runtime divisor d >= 1 for numerators x < 2^31:
+// floor(x/d) = umulhi(x, m) >> sh with m = ceil(2^(31+l)/d), l = ceil(log2 d),
+// sh = l - 1; d = 1 is m = 0 (quotient x).
+struct FastDiv {
+    uint32_t m, sh;
+};
 
-// acc = 2 acc + (x >= q): the carry flag of sub.cc (the carry out of
-// x + ~q + 1, set when nothing is borrowed) appended by addc; returns x - q.
-__device__ __forceinline__ uint32_t sub_carry_into(uint32_t x, uint32_t q, uint32_t &acc)
+__device__ __forceinline__ FastDiv make_div(uint32_t d)
 {
-    uint32_t d;
-    asm("{\n\tsub.cc.u32 %0, %2, %3;\n\taddc.u32 %1, %1, %1;\n\t}" : "=r"(d), "+r"(acc) : "r"(x), "r"(q));
-    return d;
+    FastDiv f;
+    if (d <= 1) {
+        f.m = 0;
+        f.sh = 0;
+        return f;
+    }
+    const uint32_t l = 32u - __clz(d - 1u);  // ceil(log2 d)
+    const unsigned long long num = 1ull << (31 + l);
+    f.m = (uint32_t)((num + d - 1) / d);
+    f.sh = l - 1u;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, FastDiv f) { return f.m == 0 ? x : (__umulhi(x, f.m) >> f.sh); }
+
+// Shared memory by 32-bit shared-window address (the sweep's hot loads).
+__device__ __forceinline__ uint32_t lds32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lds8(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void sts8(uint32_t a, uint32_t v)
+{
+    asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
 // Term planes of one item: bit b of pl[k] is set when term k's value is
 // negative for replica b (it turns positive on a flip); without SIGN, when
-// the product of the term's spins is -1 (the per-site code tables fold the
-// weight's sign in, so the item never loads the weights).  kw[k] is K*|w_k|.
-// PAIRS: every term has exactly one other member (minor embedding);
-// otherwise absent members read the zero word of site n (branch-free).
+// the product of the term's spins is -1 (the per-site tables of minor
+// embedding fold the weight's sign in, so its items never load weights).
+// kw[k] is K*|w_k|.  PAIRS: every term has exactly one other member (minor
+// embedding); otherwise absent members read the zero word of site n.
 template <bool PAIRS, bool SIGN = true>
-__device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *row, int n, int wc, int w,
-                                            uint32_t s, uint32_t (&pl)[kMaxTerms],
-                                            uint32_t (&kw)[kMaxTerms])
+__device__ __forceinline__ void term_planes(const SiteRec &sr, uint32_t row, int n, int wc, int w, uint32_t s,
+                                            uint32_t (&pl)[kMaxTerms], uint32_t (&kw)[kMaxTerms])
 {
 #pragma unroll
     for (int k = 0; k < kMaxTerms; k++) {
@@ -155,13 +197,13 @@ __device__ __forceinline__ void term_planes(const SiteRec &sr, const uint32_t *r
             const TermRec tr = sr.t[k];
             uint32_t p = s;
             if (PAIRS) {
-                p ^= row[tr.p[0] * wc + w];
+                p ^= lds32(row + 4u * (uint32_t)(tr.p[0] * wc + w));
             } else {
                 // an absent member (-1) reads the row's zero slot at site n
                 const uint32_t z = (uint32_t)n;
-                p ^= row[min((uint32_t)(int)tr.p[0], z) * wc + w];
-                p ^= row[min((uint32_t)(int)tr.p[1], z) * wc + w];
-                p ^= row[min((uint32_t)(int)tr.p[2], z) * wc + w];
+                p ^= lds32(row + 4u * (min((uint32_t)(int)tr.p[0], z) * wc + w));
+                p ^= lds32(row + 4u * (min((uint32_t)(int)tr.p[1], z) * wc + w));
+                p ^= lds32(row + 4u * (min((uint32_t)(int)tr.p[2], z) * wc + w));
             }
             if (SIGN) {
                 const int wv = tr.w;
@@ -205,181 +247,276 @@ __device__ __forceinline__ void transpose8(uint32_t (&P)[8])
 #undef SQA_SWAP
 }
 
-// Division by a runtime divisor d >= 1 for numerators x < 2^31:
-// floor(x/d) = umulhi(x, m) >> sh with m = ceil(2^(31+l)/d), l = ceil(log2 d),
-// sh = l - 1; d = 1 is m = 0 (quotient x).
-struct FastDiv {
-    uint32_t d, m, sh;
-};
-
-__device__ __forceinline__ FastDiv make_div(uint32_t d)
-{
-    FastDiv f;
-    f.d = d;
-    if (d <= 1) {
-        f.m = 0;
-        f.sh = 0;
-        return f;
-    }
-    const uint32_t l = 32u - __clz(d - 1u);  // ceil(log2 d)
-    const unsigned long long num = 1ull << (31 + l);
-    f.m = (uint32_t)((num + d - 1) / d);
-    f.sh = l - 1u;
-    return f;
-}
-
-__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f)
-{
-    return f.m == 0 ? x : (__umulhi(x, f.m) >> f.sh);
-}
-
 // The keys of the two sweep streams.
 struct Keys {
     uint32_t k0, khi, klo;
 };
 
-// Full threshold index of a replica from its code (SQA tables: bit 0, 1 = the
-// two temporal disagreements, bit 2+k = term k negative; FOLD: bit 2+k = the
+// Full threshold index of a replica from its code (SQA: bit 0, 1 = the two
+// temporal disagreements, bit 2+k = term k negative; FOLD: bit 2+k = the
 // product of term k's spins is -1, so term k is negative when that bit
-// differs from the weight's sign bit) or its window byte.
+// differs from the weight's sign bit; PT: bit k = term k negative).
 template <int KIND, bool FOLD = false>
 __device__ __forceinline__ int full_index(const SiteRec &sr, uint32_t code)
 {
-    if (KIND == SQA_KIND_SQA) {
-        int U = 2 - (int)(code & 1u) - (int)((code >> 1) & 1u);
+    int U = KIND == SQA_KIND_SQA ? 2 - (int)(code & 1u) - (int)((code >> 1) & 1u) : 0;
+    const int sh = KIND == SQA_KIND_SQA ? 2 : 0;
+#pragma unroll
+    for (int k = 0; k < kMaxTerms; k++) {
+        if (k < sr.nterm) {
+            const int wv = sr.t[k].w;
+            const uint32_t neg = FOLD ? (((code >> (k + sh)) & 1u) ^ (uint32_t)(wv < 0)) : ((code >> (k + sh)) & 1u);
+            if (neg) U += wv < 0 ? -wv : wv;
+        }
+    }
+    return sr.base + U;
+}
+
+// The compare of one item, four replicas per word: X_j holds the 7-bit high
+// parts h of replicas (j, j+8, j+16, j+24) under a guard bit in its four
+// bytes, Q_j the top 7 bits of their thresholds (T >> 25).  Per byte,
+// D = (128 + h) - (T >> 25) never borrows, and its bit 7 is set iff
+// h >= T >> 25; D - 1 has bit 7 set iff h > T >> 25.  Gathered over the
+// eight words (bit 8b + j for replica j + 8b), ge marks the replicas whose
+// high part decides reject or is tied, gt those that reject outright; ties
+// (ge and not gt, probability 2^-7) are resolved from the low 25 bits.
+__device__ __forceinline__ void swar_compare(const U4 &A0, const U4 &A1, const uint32_t (&Q)[8], uint32_t &ge,
+                                             uint32_t &gt)
+{
+    const uint32_t H = 0x80808080u;
+    ge = 0u;
+    gt = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const uint32_t x = word_of(j < 4 ? A0 : A1, j & 3) | H;
+        const uint32_t d1 = x - Q[j];
+        const uint32_t d2 = d1 - 0x01010101u;
+        ge = (ge >> 1) | (d1 & H);
+        gt = (gt >> 1) | (d2 & H);
+    }
+}
+
+// Four table bytes gathered into one word: byte b from the entry at the
+// shared address formed by code byte b under the slot's aligned base.
+__device__ __forceinline__ uint32_t gather_lut(uint32_t code, uint32_t slot)
+{
+    const uint32_t t0 = lds8(__byte_perm(code, slot, 0x7650u));
+    const uint32_t t1 = lds8(__byte_perm(code, slot, 0x7651u));
+    const uint32_t t2 = lds8(__byte_perm(code, slot, 0x7652u));
+    const uint32_t t3 = lds8(__byte_perm(code, slot, 0x7653u));
+    return (t3 * 256u + t2) * 65536u + (t1 * 256u + t0);
+}
+
+// Four threshold bytes of a window: byte b from base + byte b of the index word.
+__device__ __forceinline__ uint32_t gather_window(uint32_t idx, uint32_t base)
+{
+    const uint32_t t0 = lds8(base + (idx & 0xFFu));
+    const uint32_t t1 = lds8(base + __byte_perm(idx, 0u, 0x4441u));
+    const uint32_t t2 = lds8(base + __byte_perm(idx, 0u, 0x4442u));
+    const uint32_t t3 = lds8(base + (idx >> 24));
+    return (t3 * 256u + t2) * 65536u + (t1 * 256u + t0);
+}
+
+// Everything an item of one task needs besides its slice or slot.
+struct Task {
+    int si, w, gw, wc;     // site, word in the unit, global word, words of the unit
+    uint32_t own;          // byte offset of the item's word in a row
+    uint32_t nb[kMaxTerms];  // PAIRS: byte offsets of the neighbours' words (absent: own, a zero plane)
+    uint32_t slot0;        // canonical site * Z (random-number counter)
+    uint32_t lut;          // SQA table mode: shared address of the site's table
+    uint32_t swz;          // SQA table mode: the site's code swizzle (lut_swizzle)
+    uint32_t valid;        // replicas of the word that exist
+};
+
+// The planes of an item and, for SQA, its temporal disagreement words.  NB:
+// the task holds the neighbours' offsets (minor embedding with sign-folded
+// tables); otherwise they come from the site record.
+template <int KIND, bool PAIRS, bool SIGN, bool NB>
+__device__ __forceinline__ void item_planes(const JobDev &J, const Smem &sm, const Part &pt, const Task &tk,
+                                            const SiteRec &sr, int zl, uint32_t &s, uint32_t (&pl)[kMaxTerms],
+                                            uint32_t (&kw)[kMaxTerms], uint32_t &d1, uint32_t &d2)
+{
+    const uint32_t S0 = saddr(sm.S), zs4 = 4u * (uint32_t)J.zstride;
+    const uint32_t row = S0 + (uint32_t)zl * zs4;
+    s = lds32(row + tk.own);
+    if (NB) {
+        // minor embedding, sign-folded tables: the task's neighbour offsets
 #pragma unroll
         for (int k = 0; k < kMaxTerms; k++) {
-            if (FOLD) {
-                if (k < sr.nterm) {
-                    const int wv = sr.t[k].w;
-                    if (((code >> (k + 2)) & 1u) ^ (uint32_t)(wv < 0)) U += wv < 0 ? -wv : wv;
-                }
-            } else if (k < sr.nterm && ((code >> (k + 2)) & 1u)) {
-                const int wv = sr.t[k].w;
-                U += wv < 0 ? -wv : wv;
-            }
+            pl[k] = s ^ lds32(row + tk.nb[k]);
+            kw[k] = 0u;
         }
-        return sr.base + U;
+    } else {
+        term_planes<PAIRS, SIGN>(sr, row, J.n, tk.wc, tk.w, s, pl, kw);
     }
-    return sr.base + (int)code;
-}
-
-// One item: the word of 32 replicas of site si at local slice/slot zl.  Byte r
-// of code[j] selects replica j + 8r's threshold: a per-site table entry (SQA,
-// table mode) or an index in the site's window of the threshold row.
-template <int KIND, bool LUT, bool PAIRS = false, bool FOLD = false>
-__device__ __forceinline__ void sweep_item(const JobDev &J, const Keys &K, const Smem &sm, const Part &pt,
-                                           int inst, int w0, int wc, int t, int si, int zl, int w)
-{
-    const SiteRec &sr = sm.sites[si];
-    uint32_t *row = sm.S + (size_t)zl * J.zstride;
-    const int idx = si * wc + w;
-    const uint32_t s = row[idx];
-    const int z = pt.z0 + zl;  // global slice / slot
-    uint32_t code[8];
-    {
-        uint32_t pl[kMaxTerms], kw[kMaxTerms];
-        term_planes<PAIRS, !FOLD>(sr, row, J.n, wc, w, s, pl, kw);
-        uint32_t d1 = 0u, d2 = 0u;
-        if (KIND == SQA_KIND_SQA) {
-            // temporal disagreements: m = sigma (sigma_up + sigma_dn) = 2 - 2 (d1 + d2)
-            if (zl > 0)
-                d1 = s ^ sm.S[(size_t)(zl - 1) * J.zstride + idx];
-            else if (pt.C > 1)
-                d1 = s ^ pt.up[idx];
-            else
-                d1 = s ^ sm.S[(size_t)(pt.zr - 1) * J.zstride + idx];
-            if (zl < pt.zr - 1)
-                d2 = s ^ sm.S[(size_t)(zl + 1) * J.zstride + idx];
-            else if (pt.C > 1)
-                d2 = s ^ pt.dn[idx];
-            else
-                d2 = s ^ sm.S[idx];
-        }
-        if (KIND == SQA_KIND_SQA && LUT) {
-            code[0] = d1;
-            code[1] = d2;
-#pragma unroll
-            for (int k = 0; k < kMaxTerms; k++) code[k + 2] = pl[k];
-            transpose8(code);
+    d1 = d2 = 0u;
+    if (KIND == SQA_KIND_SQA) {
+        // temporal disagreements: m = sigma (sigma_up + sigma_dn) = 2 - 2 (d1 + d2)
+        uint32_t up, dn;
+        if (pt.C == 1) {
+            // one block holds the whole ring: the rows wrap around (selects, no branches)
+            const uint32_t ur = zl > 0 ? row - zs4 : S0 + (uint32_t)(pt.zr - 1) * zs4;
+            const uint32_t dr = zl < pt.zr - 1 ? row + zs4 : S0;
+            up = lds32(ur + tk.own);
+            dn = lds32(dr + tk.own);
         } else {
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                uint32_t a = window4(pl, kw, j);
-                if (KIND == SQA_KIND_SQA) a += 0x02020202u - bytes4(d1, j) - bytes4(d2, j);
-                code[j] = a;
-            }
+            if (zl > 0)
+                up = lds32(row - zs4 + tk.own);
+            else
+                up = pt.up[tk.own >> 2];
+            if (zl < pt.zr - 1)
+                dn = lds32(row + zs4 + tk.own);
+            else
+                dn = pt.dn[tk.own >> 2];
         }
+        d1 = s ^ up;
+        d2 = s ^ dn;
     }
-    const int32_t *Q = (KIND == SQA_KIND_SQA && LUT) ? sm.lut + sr.lut_off
-                       : (KIND == SQA_KIND_SQA ? sm.Tq + sr.base : sm.Tq + (size_t)zl * J.nrow + sr.base);
-    const uint32_t *Tfull = KIND == SQA_KIND_SQA ? sm.T : sm.T + (size_t)zl * J.nrow;
-    const int gw = w0 + w;
-    const uint32_t slot = (uint32_t)(sr.canon * J.Z + z);
-    const uint32_t g0 = (uint32_t)gw * 4u;
-    // the four Philox blocks first (independent chains the scheduler can
-    // interleave), then the 32 compares; ties are fixed after all of them
-    U4 Ar[4];
-#pragma unroll
-    for (int r = 0; r < 4; r++) Ar[r] = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.khi);
-    uint32_t rej = 0u;  // bit 8r + j: replica j + 8r rejects
-    bool tie = false;
-#pragma unroll
-    for (int r = 3; r >= 0; r--) {
-#pragma unroll
-        for (int j = 7; j >= 0; j--) {
-            const int32_t q = Q[__byte_perm(code[j], 0u, 0x4440u + (uint32_t)r)];
-            const uint32_t aw = word_of(Ar[r], j >> 1);
-            // the replica's 16 high uniform bits at the top of x (an odd
-            // replica's low neighbour bits below them do not change x >= q)
-            const uint32_t x = (j & 1) ? aw : (aw << 16);
-            const uint32_t d = sub_carry_into(x, (uint32_t)q, rej);  // append the reject bit
-            tie |= d < 0x10000u;
-        }
-    }
-    if (tie) {
-        // high halves equal (probability 2^-16 per replica): redraw the
-        // block, draw the low halves and compare whole uniforms with whole
-        // thresholds (the blocks are recomputed so they need not stay live)
-#pragma unroll 1
-        for (int r = 0; r < 4; r++) {
-            const U4 A2 = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.khi);
-            const U4 B2 = philox((uint32_t)t, slot, g0 + (uint32_t)r, (uint32_t)inst, K.k0, K.klo);
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const uint32_t c = __byte_perm(code[j], 0u, 0x4440u + (uint32_t)r);
-                const uint32_t aw = word_of(A2, j >> 1);
-                const uint32_t x = (j & 1) ? aw : (aw << 16);
-                const uint32_t d = x - (uint32_t)Q[c];
-                if (d < 0x10000u) {
-                    const uint32_t sh = 16u * (uint32_t)(j & 1);
-                    uint32_t u = ((aw >> sh) & 0xFFFFu) << 16 | ((word_of(B2, j >> 1) >> sh) & 0xFFFFu);
-                    u = u < 0xFFFFFFFEu ? u : 0xFFFFFFFEu;
-                    const uint32_t T = Tfull[LUT ? full_index<KIND, FOLD>(sr, c) : sr.base + (int)c];
-                    const uint32_t bit = 1u << (8 * r + j);
-                    if (u < T)
-                        rej &= ~bit;
-                    else
-                        rej |= bit;
-                }
-            }
-        }
-    }
-    row[idx] = s ^ (~rej & valid_bits(J.R, gw));
 }
 
-// SQA: per-site tables for sweep t from the staged threshold row: entry c is
-// the high half (T & 0xFFFF0000) of T[base + 2 + sum of K|w_k| over the
-// negative terms - the two temporal bits], term k negative when code bit 2+k
-// is set (FOLD: when it, the spin product being -1, differs from the sign of
-// w_k).
+// Resolves the tied replicas (mask tm) of the item at slice or slot zl:
+// their high parts equal their thresholds' top 7 bits, so each accepts iff
+// its low 25 bits (SWEEP_LO stream) are below the threshold's low 25 bits,
+// or the threshold stands for x <= 0.  The item's planes are recomputed
+// from the state (the phase changes no neighbour of it, and its tied bits
+// are still unflipped).
+template <int KIND, bool LUT, bool PAIRS>
+__device__ __forceinline__ void resolve_ties(const JobDev &J, const Smem &sm, const Part &pt, int inst, int w0,
+                                             int wc, int t, int si, int zl, int w, uint32_t tm)
+{
+    constexpr bool FOLD = KIND == SQA_KIND_SQA && LUT && PAIRS;
+    const SiteRec &sr = sm.sites[si];
+    Task tk;
+    tk.si = si;
+    tk.w = w;
+    tk.wc = wc;
+    tk.own = 4u * (uint32_t)(si * wc + w);
+    if (FOLD)
+#pragma unroll
+        for (int k = 0; k < kMaxTerms; k++) {
+            const int p = sr.t[k].p[0];
+            tk.nb[k] = 4u * (uint32_t)((p < 0 ? si : p) * wc + w);
+        }
+    uint32_t s, pl[kMaxTerms], kw[kMaxTerms], d1, d2;
+    item_planes<KIND, PAIRS, !FOLD, FOLD>(J, sm, pt, tk, sr, zl, s, pl, kw, d1, d2);
+    const uint32_t gw = (uint32_t)(w0 + w);
+    const uint32_t slot = (uint32_t)sr.canon * (uint32_t)J.Z + (uint32_t)(pt.z0 + zl);
+    const uint32_t *Trow = KIND == SQA_KIND_SQA ? sm.T : sm.T + (size_t)zl * J.nrow;
+    uint32_t flip = 0u;
+    while (tm) {
+        const int b = __ffs(tm) - 1;
+        tm &= tm - 1u;
+        // threshold index: base + the temporal part (SQA) + K|w| of each
+        // term that turns positive
+        int U = sr.base;
+        if (KIND == SQA_KIND_SQA) U += 2 - (int)((d1 >> b) & 1u) - (int)((d2 >> b) & 1u);
+#pragma unroll
+        for (int k = 0; k < kMaxTerms; k++) {
+            const int wv = sr.t[k].w;
+            const uint32_t neg = ((pl[k] >> b) & 1u) ^ (FOLD ? (uint32_t)wv >> 31 : 0u);
+            U += neg ? (wv < 0 ? -wv : wv) : 0;
+        }
+        const uint32_t T = Trow[U];
+        const uint32_t rho = gw * 32u + (uint32_t)b;
+        const U4 B = philox_rk((uint32_t)t, slot, rho >> 2, (uint32_t)inst, J.rk0, J.rk_lo);
+        const uint32_t r = rho & 3u;
+        const uint32_t l = (r == 0 ? B.x : r == 1 ? B.y : r == 2 ? B.z : B.w) >> 7;
+        if (T == 0xFFFFFFFFu || l < (T & 0x1FFFFFFu)) flip |= 1u << b;
+    }
+    const uint32_t a = saddr(sm.S) + (uint32_t)zl * 4u * (uint32_t)J.zstride + tk.own;
+    sts32(a, lds32(a) ^ flip);
+}
+
+// A tie-queue entry: the item's word in the block's state (slice or slot
+// row, then site and word) and its tie mask.
+__device__ __forceinline__ uint2 tie_entry(const JobDev &J, const Task &tk, int zl, uint32_t tm)
+{
+    return make_uint2((uint32_t)zl * (uint32_t)J.zstride + (tk.own >> 2), tm);
+}
+
+// One item: the word of 32 replicas of the task's site at local slice or
+// slot zl.  Draws the two SWEEP_HI blocks of the word, forms per replica the
+// threshold index (a per-site table entry by code, or a window index), and
+// compares four replicas per instruction; flips the replicas whose high
+// parts accept, and returns the tie mask (ties are left unflipped).
+template <int KIND, bool LUT, bool PAIRS>
+__device__ __forceinline__ uint32_t metro_item(const JobDev &J, const Keys &K, const Smem &sm, const Part &pt,
+                                               const Task &tk, const SiteRec &sr, int inst, int t, int zl)
+{
+    constexpr bool FOLD = KIND == SQA_KIND_SQA && LUT && PAIRS;
+    uint32_t s, pl[kMaxTerms], kw[kMaxTerms], d1, d2;
+    item_planes<KIND, PAIRS, !FOLD, FOLD>(J, sm, pt, tk, sr, zl, s, pl, kw, d1, d2);
+    const uint32_t slot = tk.slot0 + (uint32_t)(pt.z0 + zl);
+    // the word's two SWEEP_HI blocks: 16 bytes each, one per replica
+    const U4 A0 = philox_rk((uint32_t)t, slot, 2u * (uint32_t)tk.gw, (uint32_t)inst, J.rk0, J.rk_hi);
+    const U4 A1 = philox_rk((uint32_t)t, slot, 2u * (uint32_t)tk.gw + 1u, (uint32_t)inst, J.rk0, J.rk_hi);
+    uint32_t Q[8];
+    if (KIND == SQA_KIND_SQA && LUT) {
+        uint32_t code[8];
+        code[0] = d1;
+        code[1] = d2;
+#pragma unroll
+        for (int k = 0; k < kMaxTerms; k++) code[k + 2] = pl[k];
+        // code bits 4-6 swizzled by the site (the table stores entry c at c ^ swz)
+        code[4] ^= 0u - (tk.swz >> 4 & 1u);
+        code[5] ^= 0u - (tk.swz >> 5 & 1u);
+        code[6] ^= 0u - (tk.swz >> 6 & 1u);
+        transpose8(code);
+#pragma unroll
+        for (int j = 0; j < 8; j++) Q[j] = gather_lut(code[j], tk.lut);
+    } else {
+        const uint32_t wb = saddr(KIND == SQA_KIND_SQA ? sm.Tb : sm.Tb + (size_t)zl * J.nrow) + (uint32_t)sr.base;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            uint32_t a = window4(pl, kw, j);
+            if (KIND == SQA_KIND_SQA) a += 0x02020202u - bytes4(d1, j) - bytes4(d2, j);
+            Q[j] = gather_window(a, wb);
+        }
+    }
+    uint32_t ge, gt;
+    swar_compare(A0, A1, Q, ge, gt);
+    const uint32_t S0 = saddr(sm.S);
+    sts32(S0 + (uint32_t)zl * 4u * (uint32_t)J.zstride + tk.own, s ^ (~ge & tk.valid));
+    return ge & ~gt & tk.valid;
+}
+
+// Puts the tied items of the warp's active lanes on the block's queue: one
+// atomic per warp, each lane with ties writes its entry at its rank among
+// them.  The queue holds every item of a phase, so it cannot fill.
+__device__ __forceinline__ void queue_ties(const JobDev &J, const Smem &sm, const Task &tk, int zl, uint32_t tm,
+                                           uint32_t *qn)
+{
+    const uint32_t act = __activemask();
+    const uint32_t bal = __ballot_sync(act, tm != 0u);
+    if (bal == 0u) return;
+    const int lane = (int)(threadIdx.x & 31u), leader = __ffs(bal) - 1;
+    uint32_t base = 0u;
+    if (lane == leader) base = atomicAdd(qn, (uint32_t)__popc(bal));
+    base = __shfl_sync(act, base, leader);
+    if (tm) sm.q[base + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = tie_entry(J, tk, zl, tm);
+}
+
+// Where a site's table keeps the entry of code c: at byte c ^ swz of its
+// slot.  The slots are 256-byte aligned, so without it the same code of
+// different sites would fall on the same shared-memory bank; the lanes of a
+// warp work on up to eight sites (consecutive lanes take consecutive words
+// of one site), and XOR-ing code bits 4-6 with the site's low three bits
+// moves each site's entries by 4 (site % 8) banks.
+__device__ __forceinline__ uint32_t lut_swizzle(int si) { return ((uint32_t)si & 7u) << 4; }
+
+// SQA: per-site byte tables for sweep t from the staged threshold row:
+// entry c is the top 7 bits (T >> 25) of T[base + 2 + sum of K|w_k| over
+// the negative terms - the two temporal bits], term k negative when code
+// bit 2+k is set (FOLD: when it, the spin product being -1, differs from
+// the sign of w_k).  Only the 2^(nterm+2) codes a site can produce are
+// written.
 template <bool FOLD>
 __device__ void build_luts(const JobDev &J, const Smem &sm)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int si = warp; si < J.n; si += nw) {
         const SiteRec &sr = sm.sites[si];
-        const int nt = sr.nterm, base = sr.base, off = sr.lut_off;
+        const int nt = sr.nterm, base = sr.base;
         // the site's weights once, in registers (entries are independent)
         int aw[kMaxTerms];
         uint32_t flip[kMaxTerms];
@@ -390,13 +527,14 @@ __device__ void build_luts(const JobDev &J, const Smem &sm)
             flip[k] = FOLD ? (uint32_t)(wv < 0) : 0u;
         }
         const int ne = 1 << (nt + 2);
+        const uint32_t slot = sm.lut + (uint32_t)si * kLutSlot, swz = lut_swizzle(si);
         for (int c = lane; c < ne; c += 32) {
             // as full_index: bits of terms k >= nt are 0 and their weights 0
             int U = 2 - (c & 1) - ((c >> 1) & 1);
 #pragma unroll
             for (int k = 0; k < kMaxTerms; k++)
                 if ((((uint32_t)c >> (k + 2)) & 1u) ^ flip[k]) U += aw[k];
-            sm.lut[off + c] = high_part(sm.T[base + U]);
+            sts8(slot + ((uint32_t)c ^ swz), sm.T[base + U] >> 25);
         }
     }
 }
@@ -837,9 +975,29 @@ __device__ void run_unit_wolff(const JobDev &J, const Smem &sm, const Unit &u)
     __syncthreads();
 }
 
-template <int KIND, bool LUT, bool PAIRS = false, bool FOLD = false>
+// Slices (SQA: slice pairs) or slots per task for one colour phase of
+// `pairs` (site, word) pairs and zn slice steps: the chunk whose longest
+// thread runs the fewest items (ties to the longer chunk, at most 8), so a
+// task's site record is read once for several items.
+__device__ __forceinline__ int chunk_for(int pairs, int zn, int nthr)
+{
+    int best_c = 1;
+    long long best = -1;
+    for (int c = 1; c <= 8 && c <= zn; c++) {
+        const long long tasks = (long long)pairs * ((zn + c - 1) / c);
+        const long long cost = (tasks + nthr - 1) / nthr * c;
+        if (best < 0 || cost <= best) {
+            best = cost;
+            best_c = c;
+        }
+    }
+    return best_c;
+}
+
+template <int KIND, bool LUT, bool PAIRS>
 __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 {
+    constexpr bool FOLD = KIND == SQA_KIND_SQA && LUT && PAIRS;
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int Z = J.Z, n = J.n, wc = u.wc, inst = u.inst, w0 = u.w0;
     const Keys K{J.seed_lo, J.key_hi, J.key_lo};
@@ -872,49 +1030,92 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
         for (int i = tid; i < zr * J.nrow; i += nthr) {
             const uint32_t T = J.T[(size_t)z0 * J.nrow + i];
             sm.T[i] = T;
-            sm.Tq[i] = high_part(T);
+            sm.Tb[i] = (uint8_t)(T >> 25);
         }
+    if (tid < 2) sm.qn[tid] = 0u;
+    if (tid < J.ncol) {
+        const FastDiv f = make_div((uint32_t)(J.col_ptr[tid + 1] - J.col_ptr[tid]));
+        sm.qdiv[2 * tid] = f.m;
+        sm.qdiv[2 * tid + 1] = f.sh;
+    }
+    const FastDiv div_wc = make_div((uint32_t)wc), div_zs = make_div((uint32_t)J.zstride);
     cluster_barrier(pt.C);
-    const FastDiv div_w = make_div((uint32_t)wc);
-    const FastDiv div_z = make_div((uint32_t)(KIND == SQA_KIND_SQA ? (zr >> 1) : zr));
+    const int zn = KIND == SQA_KIND_SQA ? (zr >> 1) : zr;
+    int cz[kMaxColours];
+#pragma unroll
+    for (int c = 0; c < kMaxColours; c++)
+        cz[c] = c < J.ncol ? chunk_for((J.col_ptr[c + 1] - J.col_ptr[c]) * wc, zn, nthr) : 1;
 
+    int ph = 0;  // running phase index: the tie queue counters alternate
     for (int t = J.t0; t < J.t1; t++) {
         if (KIND == SQA_KIND_SQA) {
             for (int i = tid; i < J.nrow; i += nthr) {
                 const uint32_t T = __ldg(J.T + (size_t)t * J.nrow + i);
                 sm.T[i] = T;
-                if (!LUT) sm.Tq[i] = high_part(T);
+                if (!LUT) sm.Tb[i] = (uint8_t)(T >> 25);
             }
             __syncthreads();
             if (LUT) {
                 build_luts<FOLD>(J, sm);
                 __syncthreads();
             }
-            const int half = zr >> 1;
-            for (int cls = 0; cls < 2 * J.ncol; cls++) {
-                const int chi = cls >> 1, par = cls & 1;
-                const int c0 = J.col_ptr[chi];
-                const int nitems = (J.col_ptr[chi + 1] - c0) * half * wc;
-                for (int it = tid; it < nitems; it += nthr) {
-                    const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
-                    const int q = (int)fdiv((uint32_t)r, div_z), zh = r - q * half;
-                    sweep_item<SQA_KIND_SQA, LUT, PAIRS, FOLD>(J, K, sm, pt, inst, w0, wc, t, c0 + q, 2 * zh + par, w);
-                }
-                cluster_barrier(pt.C);  // neighbouring blocks read this phase's boundary slices
-            }
-        } else {
-            for (int chi = 0; chi < J.ncol; chi++) {
-                const int c0 = J.col_ptr[chi];
-                const int nitems = (J.col_ptr[chi + 1] - c0) * zr * wc;
-                for (int it = tid; it < nitems; it += nthr) {
-                    const int r = (int)fdiv((uint32_t)it, div_w), w = it - r * wc;
-                    const int q = (int)fdiv((uint32_t)r, div_z), p = r - q * zr;
-                    sweep_item<SQA_KIND_PT, false, PAIRS>(J, K, sm, pt, inst, w0, wc, t, c0 + q, p, w);
-                }
-                __syncthreads();
-            }
-            if (Z > 1 && (t + 1) % J.swap_every == 0) pt_swap(J, sm, pt, inst, w0, wc, (t + 1) / J.swap_every - 1);
         }
+        const int nph = KIND == SQA_KIND_SQA ? 2 * J.ncol : J.ncol;
+        for (int cls = 0; cls < nph; cls++, ph++) {
+            const int chi = KIND == SQA_KIND_SQA ? cls >> 1 : cls, par = KIND == SQA_KIND_SQA ? cls & 1 : 0;
+            const int c0 = J.col_ptr[chi], nq = J.col_ptr[chi + 1] - c0;
+            int czc = cz[0];
+#pragma unroll
+            for (int c = 1; c < kMaxColours; c++)
+                if (chi == c) czc = cz[c];
+            const int ntasks = nq * wc * ((zn + czc - 1) / czc);
+            const FastDiv div_nq{sm.qdiv[2 * chi], sm.qdiv[2 * chi + 1]};
+            uint32_t *qn = sm.qn + (ph & 1);
+            for (int tau = tid; tau < ntasks; tau += nthr) {
+                const int r = (int)fdiv((uint32_t)tau, div_wc), w = tau - r * wc;
+                const int ch = (int)fdiv((uint32_t)r, div_nq), q = r - ch * nq;
+                const int si = c0 + q;
+                const SiteRec &sr = sm.sites[si];
+                Task tk;
+                tk.si = si;
+                tk.w = w;
+                tk.gw = w0 + w;
+                tk.wc = wc;
+                tk.own = 4u * (uint32_t)(si * wc + w);
+                tk.slot0 = (uint32_t)sr.canon * (uint32_t)Z;
+                tk.valid = valid_bits(J.R, tk.gw);
+                tk.lut = sm.lut + (uint32_t)si * kLutSlot;
+                tk.swz = lut_swizzle(si);
+                if (FOLD) {
+                    const int nt = sr.nterm;
+#pragma unroll
+                    for (int k = 0; k < kMaxTerms; k++)
+                        tk.nb[k] = k < nt ? 4u * (uint32_t)(sr.t[k].p[0] * wc + w) : tk.own;
+                }
+                const int zlo = ch * czc, zhi = min(zn, zlo + czc);
+                for (int zz = zlo; zz < zhi; zz++) {
+                    const int zl = KIND == SQA_KIND_SQA ? 2 * zz + par : zz;
+                    const uint32_t tm = metro_item<KIND, LUT, PAIRS>(J, K, sm, pt, tk, sr, inst, t, zl);
+                    queue_ties(J, sm, tk, zl, tm, qn);
+                }
+            }
+            __syncthreads();  // the phase's queue is complete
+            const uint32_t nties = *qn;
+            if (tid == 0) sm.qn[(ph + 1) & 1] = 0u;  // the next phase's counter (last read a phase ago)
+            for (uint32_t e = tid; e < nties; e += nthr) {
+                const uint2 en = sm.q[e];
+                const uint32_t zl = fdiv(en.x, div_zs), rem = en.x - zl * (uint32_t)J.zstride;
+                const uint32_t si = fdiv(rem, div_wc);
+                resolve_ties<KIND, LUT, PAIRS>(J, sm, pt, inst, w0, wc, t, (int)si, (int)zl, (int)(rem - si * (uint32_t)wc),
+                                               en.y);
+            }
+            if (KIND == SQA_KIND_SQA)
+                cluster_barrier(pt.C);  // neighbouring blocks read this phase's boundary slices
+            else
+                __syncthreads();
+        }
+        if (KIND == SQA_KIND_PT && Z > 1 && (t + 1) % J.swap_every == 0)
+            pt_swap(J, sm, pt, inst, w0, wc, (t + 1) / J.swap_every - 1);
     }
     for (int i = tid; i < zr * n * wc; i += nthr) {
         const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
@@ -947,19 +1148,19 @@ __global__ void __launch_bounds__(MODE == 0 || MODE == 6 ? 384 : 256, MODE == 3 
     for (int ui = cid; ui < n_units; ui += ncl) {
         const Unit u = units[ui];
         if (MODE == 0)
-            run_unit<SQA_KIND_PT, false>(J, sm, u);
+            run_unit<SQA_KIND_PT, false, false>(J, sm, u);
         else if (MODE == 6)
             run_unit<SQA_KIND_PT, false, true>(J, sm, u);
         else if (MODE == 2)
-            run_unit<SQA_KIND_SQA, true>(J, sm, u);
+            run_unit<SQA_KIND_SQA, true, false>(J, sm, u);
         else if (MODE == 5)
-            run_unit<SQA_KIND_SQA, true, true, true>(J, sm, u);
+            run_unit<SQA_KIND_SQA, true, true>(J, sm, u);
         else if (MODE == 3)
             run_unit_wolff<2>(J, sm, u);
         else if (MODE == 4)
             run_unit_wolff<4>(J, sm, u);
         else
-            run_unit<SQA_KIND_SQA, false>(J, sm, u);
+            run_unit<SQA_KIND_SQA, false, false>(J, sm, u);
     }
 }
 
@@ -1065,7 +1266,7 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const
         if (s_job.kind == SQA_KIND_PT && s_job.pairs)
             run_unit<SQA_KIND_PT, false, true>(s_job, sm, u);
         else if (s_job.kind == SQA_KIND_PT)
-            run_unit<SQA_KIND_PT, false>(s_job, sm, u);
+            run_unit<SQA_KIND_PT, false, false>(s_job, sm, u);
         else if (s_job.move == SQA_MOVE_WOLFF && s_job.Z <= 64)
             run_unit_wolff<2>(s_job, sm, u);
         else if (s_job.move == SQA_MOVE_WOLFF)
@@ -1073,9 +1274,9 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const
         else if (s_job.use_lut && s_job.pairs)
             run_unit<SQA_KIND_SQA, true, true>(s_job, sm, u);
         else if (s_job.use_lut)
-            run_unit<SQA_KIND_SQA, true>(s_job, sm, u);
+            run_unit<SQA_KIND_SQA, true, false>(s_job, sm, u);
         else
-            run_unit<SQA_KIND_SQA, false>(s_job, sm, u);
+            run_unit<SQA_KIND_SQA, false, false>(s_job, sm, u);
         __syncthreads();
     }
 }

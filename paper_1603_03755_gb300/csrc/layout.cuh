@@ -13,18 +13,36 @@
 
 namespace sqa {
 
+// Per-site byte tables of the single-spin sweep: one 256-byte slot per site,
+// each starting on a 256-byte boundary of the shared window, so that a
+// replica's 8-bit code placed in the low byte of the slot's address is the
+// entry's address.
+constexpr int kLutSlot = 256;
+
 struct SmemOffsets {
     size_t S;      // state [zr][zstride] words (this block's slices or slots; word n*wc.. of a row: zero slot)
     size_t T;      // full thresholds: SQA one row, PT P rows
-    size_t Tq;     // high halves of the thresholds (T & 0xFFFF0000): PT P rows, SQA window mode one row
-    size_t lut;    // SQA: per-site tables of threshold high halves
+    size_t Tb;     // top 7 bits of the thresholds (T >> 25), bytes: PT P rows, SQA window mode one row
+    size_t lut;    // SQA table mode: per-site byte tables (n slots of kLutSlot, plus alignment slack)
     size_t sites;  // SiteRec [n]
     size_t E;      // PT: energies [P][wc*32]
     size_t M;      // PT: swap masks [P/2+1][wc]; cluster moves: per-warp start masks [8][64 or 128]
+    size_t Q;      // 64 bytes: two tie-queue counters, and per colour the divisor of the task decode
     size_t total;
 };
 
 SQA_LHD size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Items of one colour phase of a block (SQA: colour x slice parity; PT:
+// colour), at most: every one of them may tie (two equal 7-bit high parts,
+// probability 1 - (127/128)^32 = 0.222 for a full word), so this many
+// entries of the block's tie queue hold any phase.
+SQA_LHD int tie_items(const JobDev &J, int wc)
+{
+    int nq = 0;
+    for (int c = 0; c < J.ncol; c++) nq = J.col_ptr[c + 1] - J.col_ptr[c] > nq ? J.col_ptr[c + 1] - J.col_ptr[c] : nq;
+    return nq * (J.kind == SQA_KIND_SQA ? (J.zr + 1) / 2 : J.zr) * wc;
+}
 
 SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
 {
@@ -34,8 +52,8 @@ SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
     off += (size_t)J.zr * zstride * 4;
     if (J.kind == SQA_KIND_SQA && J.move == SQA_MOVE_WOLFF) {
         // cluster moves: the state, the site records and, per warp, the
-        // start masks of one ring (M): no threshold rows or tables
-        o.T = o.Tq = o.lut = off;
+        // start masks of one ring (M): no threshold rows, tables or queue
+        o.T = o.Tb = o.lut = o.Q = off;
         off = align16(off);
         o.sites = off;
         off += (size_t)J.n * sizeof(SiteRec);
@@ -47,13 +65,14 @@ SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
     }
     o.T = off;
     off += (size_t)(J.kind == SQA_KIND_SQA ? J.nrow : J.zr * J.nrow) * 4;
-    o.Tq = off;
+    o.Tb = off;
     if (J.kind == SQA_KIND_PT)
-        off += (size_t)J.zr * J.nrow * 4;
+        off += (size_t)J.zr * J.nrow;
     else if (!J.use_lut)
-        off += (size_t)J.nrow * 4;
+        off += (size_t)J.nrow;
+    off = align16(off);
     o.lut = off;
-    if (J.kind == SQA_KIND_SQA && J.use_lut) off += (size_t)J.lut_entries * 4;
+    if (J.kind == SQA_KIND_SQA && J.use_lut) off += (size_t)(J.n + 1) * kLutSlot;
     off = align16(off);
     o.sites = off;
     off += (size_t)J.n * sizeof(SiteRec);
@@ -64,6 +83,9 @@ SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
         o.M = off;
         off += (size_t)(J.zr / 2 + 1) * wc * 4;
     }
+    off = align16(off);
+    o.Q = off;
+    off += 64;
     o.total = align16(off);
     return o;
 }

@@ -2,6 +2,7 @@
 // and the plain-old-data records the kernels read.
 #pragma once
 #include <stdint.h>
+#include <vector_types.h>  // uint2
 
 #include <string>
 #include <vector>
@@ -72,6 +73,15 @@ struct JobDev {
     uint32_t key_hi;     // seed_hi ^ kDomSweepHi
     uint32_t key_lo;     // seed_hi ^ kDomSweepLo
     uint32_t key_swap;   // seed_hi ^ kDomSwap
+    // round keys of the two sweep streams, k + r * Weyl constant for rounds
+    // r = 0..9 (first word shared: seed_lo), so the kernels read them from
+    // the parameter bank instead of forming them per block
+    uint32_t rk0[10], rk_hi[10], rk_lo[10];
+    // tie queue of the single-spin sweep in global memory: tieq_stride
+    // entries {state word, tie mask} per block (blockIdx.x), at least the
+    // items of one colour phase of a block, so the queue cannot fill
+    uint2 *tieq;
+    int tieq_stride;
     uint32_t *state;     // [I][Z][n][W]
     const SiteRec *sites;    // [I][n]
     const uint32_t *T;       // SQA [S][nrow]; PT [P][nrow]

@@ -43,26 +43,43 @@ def test_philox_key_and_counter_sensitivity():
 
 
 def test_sweep_uniform_composition():
-    """u = (SWEEP_HI half << 16) | SWEEP_LO half, halves picked by rho % 8."""
+    """u = h * 2^25 + l: h the low 7 bits of byte (r/8) of word r%4 of the
+    SWEEP_HI block at (t, slot, 2(rho/32) + (r/4)%2, inst), r = rho%32; l word
+    rho%4 of the SWEEP_LO block at (t, slot, rho/4, inst), shifted right by 7."""
     seed = 0x0123456789ABCDEF
-    for (t, slot, rho, inst) in [(0, 0, 0, 0), (7, 33, 13, 2), (99, 1000, 255, 1023)]:
-        ctr = [t, slot, rho >> 3, inst]
-        a = O.philox4x32_10(ctr, [seed & 0xFFFFFFFF, (seed >> 32) ^ DOM_SWEEP_HI])
-        b = O.philox4x32_10(ctr, [seed & 0xFFFFFFFF, (seed >> 32) ^ DOM_SWEEP_LO])
-        j = rho & 7
-        hi = (int(a[j >> 1]) >> (16 * (j & 1))) & 0xFFFF
-        lo = (int(b[j >> 1]) >> (16 * (j & 1))) & 0xFFFF
-        assert O.sweep_uniform(seed, t, slot, rho, inst) == (hi << 16) | lo
+    key_hi = [seed & 0xFFFFFFFF, (seed >> 32) ^ DOM_SWEEP_HI]
+    key_lo = [seed & 0xFFFFFFFF, (seed >> 32) ^ DOM_SWEEP_LO]
+    for (t, slot, rho, inst) in [(0, 0, 0, 0), (7, 33, 13, 2), (99, 1000, 255, 1023), (5, 6, 38, 7)]:
+        r = rho % 32
+        a = O.philox4x32_10([t, slot, 2 * (rho // 32) + (r // 4) % 2, inst], key_hi)
+        b = O.philox4x32_10([t, slot, rho // 4, inst], key_lo)
+        h = (int(a[r % 4]) >> (8 * (r // 8))) & 0x7F
+        lo = int(b[rho % 4]) >> 7
+        assert O.sweep_uniform(seed, t, slot, rho, inst) == (h << 25) | lo
+
+
+def test_sweep_uniform_streams_cover_every_replica_once():
+    """The 32 replicas of a word take 32 distinct (block, word, byte) places of
+    the two SWEEP_HI blocks, and 32 distinct (block, word) places of SWEEP_LO."""
+    hi = {(2 * (rho // 32) + (rho % 32 // 4) % 2, rho % 4, rho % 32 // 8) for rho in range(64)}
+    lo = {(rho // 4, rho % 4) for rho in range(64)}
+    assert len(hi) == 64 and len(lo) == 64
 
 
 def test_sweep_uniform_is_uniform():
     u = np.array([O.sweep_uniform(5, t, s, r, 0) for t in range(20) for s in range(10)
                   for r in range(64)], np.float64) / 2.0**32
     assert stats.kstest(u, "uniform").pvalue > 1e-3
-    # low and high halves are independent streams
-    hi = np.floor(u * 65536) / 65536
-    lo = u * 65536 - np.floor(u * 65536)
-    assert abs(np.corrcoef(hi, lo)[0, 1]) < 0.03
+    # the 7-bit high part is uniform over its 128 values
+    h = np.floor(u * 128).astype(np.int64)
+    assert stats.chisquare(np.bincount(h, minlength=128)).pvalue > 1e-3
+    # high and low parts are independent streams
+    lo = u * 128 - h
+    assert abs(np.corrcoef(h, lo)[0, 1]) < 0.03
+    # replicas of one word that share a SWEEP_HI word are not correlated
+    a = np.array([O.sweep_uniform(8, t, 3, 0, 1) for t in range(3000)], np.float64)
+    b = np.array([O.sweep_uniform(8, t, 3, 8, 1) for t in range(3000)], np.float64)
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.06
 
 
 def test_swap_uniform_is_uniform():
