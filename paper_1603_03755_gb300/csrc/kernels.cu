@@ -92,7 +92,10 @@ struct Smem {
     uint32_t *M;      // PT: swap masks [zr/2+1][wc]
     uint32_t *qn;     // tie queue counters (two, used by alternate phases)
     uint32_t *qdiv;   // per colour: the task decode's divisor {m, sh} (FastDiv)
-    uint2 *q;         // this block's tie queue entries {state word, tie mask} (global memory)
+    uint32_t *tq;     // this block's tie array: one tie mask per item of a phase (global memory)
+    uint4 *ph;        // per word of the unit and SWEEP_HI block: the sweep's hoisted Philox values
+    uint4 *rec;       // per site: the tie record (two uint4)
+    uint2 *rq;        // per warp: kRequeue entries of items with ties left after a tie pass
 };
 
 __device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -110,7 +113,10 @@ __device__ __forceinline__ Smem carve(const JobDev &J, unsigned char *base)
     m.M = (uint32_t *)(base + o.M);
     m.qn = (uint32_t *)(base + o.Q);
     m.qdiv = (uint32_t *)(base + o.Q + 16);
-    m.q = J.tieq + (size_t)blockIdx.x * (size_t)J.tieq_stride;
+    m.tq = (uint32_t *)(J.tieq + (size_t)blockIdx.x * (size_t)J.tieq_stride);
+    m.ph = (uint4 *)(base + o.P);
+    m.rec = (uint4 *)(base + o.R);
+    m.rq = (uint2 *)(base + o.RQ);
     return m;
 }
 
@@ -247,6 +253,63 @@ __device__ __forceinline__ void transpose8(uint32_t (&P)[8])
 #undef SQA_SWAP
 }
 
+// The SWEEP_HI blocks of one sweep and unit, counter (t, slot, c2, inst)
+// with t and inst fixed: c2 = 2*word + h enters through B*c2 in round 0, t
+// through A*t; the slot is XOR-ed in by round 0 and first multiplied in
+// round 1.  So per (word, h) three values fix rounds 0-2 apart from the
+// slot (P0 = hi(B c2) ^ ka0; Q2, O3 = hi(A m0) ^ kb2, lo(A m0) with m0 the
+// round-1 word that does not depend on the slot), and two values are the
+// same for the whole sweep (U2 = lo(A t) ^ kb1, U3 = lo(B n2) ^ ka2).  A
+// block then costs 16 wide multiplies instead of 20, with the same bits.
+struct PhiloxSweep {
+    uint32_t U2, U3, n2;
+};
+
+__device__ __forceinline__ PhiloxSweep philox_sweep(const JobDev &J, uint32_t t, uint32_t inst)
+{
+    uint32_t hiA, loA, hiB2, loB2;
+    mul_wide(0xD2511F53u, t, hiA, loA);
+    PhiloxSweep p;
+    p.n2 = hiA ^ inst ^ J.rk_hi[0];
+    mul_wide(0xCD9E8D57u, p.n2, hiB2, loB2);
+    p.U2 = loA ^ J.rk_hi[1];
+    p.U3 = loB2 ^ J.rk0[2];
+    return p;
+}
+
+// {P0, Q2, O3} of (word gw, block h) for the sweep (ps from philox_sweep).
+__device__ __forceinline__ uint4 philox_word(const JobDev &J, const PhiloxSweep &ps, uint32_t gw, uint32_t h)
+{
+    uint32_t hiB, loB, hiB2, loB2, hiA3, loA3;
+    mul_wide(0xCD9E8D57u, 2u * gw + h, hiB, loB);
+    mul_wide(0xCD9E8D57u, ps.n2, hiB2, loB2);
+    const uint32_t m0 = hiB2 ^ loB ^ J.rk0[1];
+    mul_wide(0xD2511F53u, m0, hiA3, loA3);
+    return make_uint4(hiB ^ J.rk0[0], hiA3 ^ J.rk_hi[2], loA3, 0u);
+}
+
+// The SWEEP_HI block of the item's slot from its word's hoisted values.
+__device__ __forceinline__ U4 philox_hi(const JobDev &J, const PhiloxSweep &ps, const uint4 &pw, uint32_t slot)
+{
+    uint32_t hiA2, loA2, hiB3, loB3;
+    mul_wide(0xD2511F53u, pw.x ^ slot, hiA2, loA2);           // round 1: A * n0
+    const uint32_t m2 = hiA2 ^ ps.U2, m3 = loA2;
+    mul_wide(0xCD9E8D57u, m2, hiB3, loB3);                    // round 2: B * m2
+    uint32_t c0 = hiB3 ^ ps.U3, c1 = loB3, c2 = pw.y ^ m3, c3 = pw.z;
+#pragma unroll
+    for (int r = 3; r < 10; r++) {
+        uint32_t hi0, lo0, hi1, lo1;
+        mul_wide(0xD2511F53u, c0, hi0, lo0);
+        mul_wide(0xCD9E8D57u, c2, hi1, lo1);
+        const uint32_t n0 = hi1 ^ c1 ^ J.rk0[r], n2 = hi0 ^ c3 ^ J.rk_hi[r];
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
 // The keys of the two sweep streams.
 struct Keys {
     uint32_t k0, khi, klo;
@@ -326,6 +389,7 @@ struct Task {
     uint32_t lut;          // SQA table mode: shared address of the site's table
     uint32_t swz;          // SQA table mode: the site's code swizzle (lut_swizzle)
     uint32_t valid;        // replicas of the word that exist
+    uint4 ph0, ph1;        // the word's hoisted SWEEP_HI values (blocks 0 and 1)
 };
 
 // The planes of an item and, for SQA, its temporal disagreement words.  NB:
@@ -374,64 +438,90 @@ __device__ __forceinline__ void item_planes(const JobDev &J, const Smem &sm, con
     }
 }
 
-// Resolves the tied replicas (mask tm) of the item at slice or slot zl:
-// their high parts equal their thresholds' top 7 bits, so each accepts iff
-// its low 25 bits (SWEEP_LO stream) are below the threshold's low 25 bits,
-// or the threshold stands for x <= 0.  The item's planes are recomputed
-// from the state (the phase changes no neighbour of it, and its tied bits
-// are still unflipped).
-template <int KIND, bool LUT, bool PAIRS>
-__device__ __forceinline__ void resolve_ties(const JobDev &J, const Smem &sm, const Part &pt, int inst, int w0,
-                                             int wc, int t, int si, int zl, int w, uint32_t tm)
+// The SWEEP_LO round keys, held in registers for a tie pass.
+struct LoKeys {
+    uint32_t a[10], b[10];
+};
+
+// A site's tie record (kTieRec bytes in shared memory): the threshold index
+// of a replica is U0 + sum_k sw_k * (bit of term plane k) minus its two
+// temporal bits (SQA).  With FOLD a plane bit is the spin product and term k
+// turns positive when it differs from the weight's sign, so a negative
+// weight counts |w| when the bit is 0: U0 takes |w| and sw_k = -|w|.  For
+// minor embedding (FOLD) the record also keeps each term's other member
+// (absent terms: the site itself, a zero plane).
+template <bool FOLD>
+__device__ __forceinline__ void tie_record(const SiteRec &sr, int si, int sqa, uint32_t *rec)
+{
+    int U0 = sr.base + (sqa ? 2 : 0), sw[kMaxTerms], p0[kMaxTerms];
+#pragma unroll
+    for (int k = 0; k < kMaxTerms; k++) {
+        const int wv = k < sr.nterm ? (int)sr.t[k].w : 0, aw = wv < 0 ? -wv : wv;
+        const bool f = FOLD && wv < 0;
+        U0 += f ? aw : 0;
+        sw[k] = f ? -aw : aw;
+        p0[k] = k < sr.nterm ? (int)sr.t[k].p[0] : si;
+    }
+    rec[0] = (uint32_t)U0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        rec[1 + k] = ((uint32_t)sw[2 * k] & 0xFFFFu) | ((uint32_t)sw[2 * k + 1] << 16);
+        rec[4 + k] = ((uint32_t)p0[2 * k] & 0xFFFFu) | ((uint32_t)p0[2 * k + 1] << 16);
+    }
+    rec[7] = 0u;
+}
+
+// Resolves ties of the item at slice or slot zl (site si, word w): the
+// lowest one of tm, or all of them when ALL.  A tied replica's high part
+// equals its threshold's top 7 bits, so it accepts iff its low 25 bits
+// (SWEEP_LO stream) are below the threshold's low 25 bits, or the threshold
+// stands for x <= 0.  The item's planes are recomputed from the state (the
+// phase changes no neighbour of it, and its tied bits are still unflipped).
+// Returns the ties left.
+template <int KIND, bool LUT, bool PAIRS, bool ALL>
+__device__ __forceinline__ uint32_t resolve_ties(const JobDev &J, const Smem &sm, const Part &pt, const LoKeys &lk,
+                                                 int inst, int w0, int wc, int t, int si, int zl, int w, uint32_t tm)
 {
     constexpr bool FOLD = KIND == SQA_KIND_SQA && LUT && PAIRS;
     const SiteRec &sr = sm.sites[si];
+    const uint4 ra = sm.rec[2 * si], rb = sm.rec[2 * si + 1];
     Task tk;
     tk.si = si;
     tk.w = w;
     tk.wc = wc;
     tk.own = 4u * (uint32_t)(si * wc + w);
-    if (FOLD)
+    if (FOLD) {
+        const uint32_t pp[3] = {rb.x, rb.y, rb.z};
 #pragma unroll
-        for (int k = 0; k < kMaxTerms; k++) {
-            const int p = sr.t[k].p[0];
-            tk.nb[k] = 4u * (uint32_t)((p < 0 ? si : p) * wc + w);
-        }
+        for (int k = 0; k < kMaxTerms; k++)
+            tk.nb[k] = 4u * ((uint32_t)(pp[k >> 1] >> (16 * (k & 1)) & 0xFFFFu) * (uint32_t)wc + (uint32_t)w);
+    }
     uint32_t s, pl[kMaxTerms], kw[kMaxTerms], d1, d2;
     item_planes<KIND, PAIRS, !FOLD, FOLD>(J, sm, pt, tk, sr, zl, s, pl, kw, d1, d2);
     const uint32_t gw = (uint32_t)(w0 + w);
     const uint32_t slot = (uint32_t)sr.canon * (uint32_t)J.Z + (uint32_t)(pt.z0 + zl);
     const uint32_t *Trow = KIND == SQA_KIND_SQA ? sm.T : sm.T + (size_t)zl * J.nrow;
+    const int U0 = (int)ra.x;
+    const uint32_t swp[3] = {ra.y, ra.z, ra.w};
     uint32_t flip = 0u;
-    while (tm) {
+    do {
         const int b = __ffs(tm) - 1;
         tm &= tm - 1u;
-        // threshold index: base + the temporal part (SQA) + K|w| of each
-        // term that turns positive
-        int U = sr.base;
-        if (KIND == SQA_KIND_SQA) U += 2 - (int)((d1 >> b) & 1u) - (int)((d2 >> b) & 1u);
+        int U = U0;
+        if (KIND == SQA_KIND_SQA) U -= (int)((d1 >> b) & 1u) + (int)((d2 >> b) & 1u);
 #pragma unroll
-        for (int k = 0; k < kMaxTerms; k++) {
-            const int wv = sr.t[k].w;
-            const uint32_t neg = ((pl[k] >> b) & 1u) ^ (FOLD ? (uint32_t)wv >> 31 : 0u);
-            U += neg ? (wv < 0 ? -wv : wv) : 0;
-        }
+        for (int k = 0; k < kMaxTerms; k++)
+            U += (int)((pl[k] >> b) & 1u) * (int)(int16_t)(swp[k >> 1] >> (16 * (k & 1)));
         const uint32_t T = Trow[U];
         const uint32_t rho = gw * 32u + (uint32_t)b;
-        const U4 B = philox_rk((uint32_t)t, slot, rho >> 2, (uint32_t)inst, J.rk0, J.rk_lo);
+        const U4 B = philox_rk((uint32_t)t, slot, rho >> 2, (uint32_t)inst, lk.a, lk.b);
         const uint32_t r = rho & 3u;
         const uint32_t l = (r == 0 ? B.x : r == 1 ? B.y : r == 2 ? B.z : B.w) >> 7;
         if (T == 0xFFFFFFFFu || l < (T & 0x1FFFFFFu)) flip |= 1u << b;
-    }
+    } while (ALL && tm);
     const uint32_t a = saddr(sm.S) + (uint32_t)zl * 4u * (uint32_t)J.zstride + tk.own;
     sts32(a, lds32(a) ^ flip);
-}
-
-// A tie-queue entry: the item's word in the block's state (slice or slot
-// row, then site and word) and its tie mask.
-__device__ __forceinline__ uint2 tie_entry(const JobDev &J, const Task &tk, int zl, uint32_t tm)
-{
-    return make_uint2((uint32_t)zl * (uint32_t)J.zstride + (tk.own >> 2), tm);
+    return tm;
 }
 
 // One item: the word of 32 replicas of the task's site at local slice or
@@ -440,16 +530,16 @@ __device__ __forceinline__ uint2 tie_entry(const JobDev &J, const Task &tk, int 
 // compares four replicas per instruction; flips the replicas whose high
 // parts accept, and returns the tie mask (ties are left unflipped).
 template <int KIND, bool LUT, bool PAIRS>
-__device__ __forceinline__ uint32_t metro_item(const JobDev &J, const Keys &K, const Smem &sm, const Part &pt,
-                                               const Task &tk, const SiteRec &sr, int inst, int t, int zl)
+__device__ __forceinline__ uint32_t metro_item(const JobDev &J, const PhiloxSweep &ps, const Smem &sm, const Part &pt,
+                                               const Task &tk, const SiteRec &sr, int zl)
 {
     constexpr bool FOLD = KIND == SQA_KIND_SQA && LUT && PAIRS;
     uint32_t s, pl[kMaxTerms], kw[kMaxTerms], d1, d2;
     item_planes<KIND, PAIRS, !FOLD, FOLD>(J, sm, pt, tk, sr, zl, s, pl, kw, d1, d2);
     const uint32_t slot = tk.slot0 + (uint32_t)(pt.z0 + zl);
     // the word's two SWEEP_HI blocks: 16 bytes each, one per replica
-    const U4 A0 = philox_rk((uint32_t)t, slot, 2u * (uint32_t)tk.gw, (uint32_t)inst, J.rk0, J.rk_hi);
-    const U4 A1 = philox_rk((uint32_t)t, slot, 2u * (uint32_t)tk.gw + 1u, (uint32_t)inst, J.rk0, J.rk_hi);
+    const U4 A0 = philox_hi(J, ps, tk.ph0, slot);
+    const U4 A1 = philox_hi(J, ps, tk.ph1, slot);
     uint32_t Q[8];
     if (KIND == SQA_KIND_SQA && LUT) {
         uint32_t code[8];
@@ -480,20 +570,15 @@ __device__ __forceinline__ uint32_t metro_item(const JobDev &J, const Keys &K, c
     return ge & ~gt & tk.valid;
 }
 
-// Puts the tied items of the warp's active lanes on the block's queue: one
-// atomic per warp, each lane with ties writes its entry at its rank among
-// them.  The queue holds every item of a phase, so it cannot fill.
-__device__ __forceinline__ void queue_ties(const JobDev &J, const Smem &sm, const Task &tk, int zl, uint32_t tm,
-                                           uint32_t *qn)
+// Stores a task's tie masks in the block's tie array: word tau * czc + i
+// for slice or slot i of task tau (0 where the item does not exist or did
+// not tie), every word of the phase written, so the array needs no counter.
+__device__ __forceinline__ void store_task_ties(const Smem &sm, int tau, int czc, const uint32_t (&tm)[kTaskSlices])
 {
-    const uint32_t act = __activemask();
-    const uint32_t bal = __ballot_sync(act, tm != 0u);
-    if (bal == 0u) return;
-    const int lane = (int)(threadIdx.x & 31u), leader = __ffs(bal) - 1;
-    uint32_t base = 0u;
-    if (lane == leader) base = atomicAdd(qn, (uint32_t)__popc(bal));
-    base = __shfl_sync(act, base, leader);
-    if (tm) sm.q[base + (uint32_t)__popc(bal & ((1u << lane) - 1u))] = tie_entry(J, tk, zl, tm);
+    uint32_t *a = sm.tq + (size_t)tau * czc;
+#pragma unroll
+    for (int i = 0; i < kTaskSlices; i++)
+        if (i < czc) a[i] = tm[i];
 }
 
 // Where a site's table keeps the entry of code c: at byte c ^ swz of its
@@ -977,13 +1062,14 @@ __device__ void run_unit_wolff(const JobDev &J, const Smem &sm, const Unit &u)
 
 // Slices (SQA: slice pairs) or slots per task for one colour phase of
 // `pairs` (site, word) pairs and zn slice steps: the chunk whose longest
-// thread runs the fewest items (ties to the longer chunk, at most 8), so a
+// thread runs the fewest items (ties to the longer chunk, at most
+// kTaskSlices, the unrolled task body), so a
 // task's site record is read once for several items.
 __device__ __forceinline__ int chunk_for(int pairs, int zn, int nthr)
 {
     int best_c = 1;
     long long best = -1;
-    for (int c = 1; c <= 8 && c <= zn; c++) {
+    for (int c = 1; c <= kTaskSlices && c <= zn; c++) {
         const long long tasks = (long long)pairs * ((zn + c - 1) / c);
         const long long cost = (tasks + nthr - 1) / nthr * c;
         if (best < 0 || cost <= best) {
@@ -1032,6 +1118,12 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
             sm.T[i] = T;
             sm.Tb[i] = (uint8_t)(T >> 25);
         }
+    for (int si = tid; si < n; si += nthr) {
+        uint32_t rec[8];
+        tie_record<FOLD>(J.sites[(size_t)inst * n + si], si, KIND == SQA_KIND_SQA, rec);
+        sm.rec[2 * si] = make_uint4(rec[0], rec[1], rec[2], rec[3]);
+        sm.rec[2 * si + 1] = make_uint4(rec[4], rec[5], rec[6], rec[7]);
+    }
     if (tid < 2) sm.qn[tid] = 0u;
     if (tid < J.ncol) {
         const FastDiv f = make_div((uint32_t)(J.col_ptr[tid + 1] - J.col_ptr[tid]));
@@ -1045,9 +1137,13 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 #pragma unroll
     for (int c = 0; c < kMaxColours; c++)
         cz[c] = c < J.ncol ? chunk_for((J.col_ptr[c + 1] - J.col_ptr[c]) * wc, zn, nthr) : 1;
+    const int warp = tid >> 5, lane = tid & 31;
+    uint2 *rq = sm.rq + (size_t)warp * kRequeue;
 
     int ph = 0;  // running phase index: the tie queue counters alternate
     for (int t = J.t0; t < J.t1; t++) {
+        const PhiloxSweep ps = philox_sweep(J, (uint32_t)t, (uint32_t)inst);
+        if (tid < 2 * wc) sm.ph[tid] = philox_word(J, ps, (uint32_t)(w0 + (tid >> 1)), (uint32_t)(tid & 1));
         if (KIND == SQA_KIND_SQA) {
             for (int i = tid; i < J.nrow; i += nthr) {
                 const uint32_t T = __ldg(J.T + (size_t)t * J.nrow + i);
@@ -1060,6 +1156,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 __syncthreads();
             }
         }
+        if (KIND == SQA_KIND_PT) __syncthreads();  // the sweep's hoisted Philox values
         const int nph = KIND == SQA_KIND_SQA ? 2 * J.ncol : J.ncol;
         for (int cls = 0; cls < nph; cls++, ph++) {
             const int chi = KIND == SQA_KIND_SQA ? cls >> 1 : cls, par = KIND == SQA_KIND_SQA ? cls & 1 : 0;
@@ -1070,7 +1167,6 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 if (chi == c) czc = cz[c];
             const int ntasks = nq * wc * ((zn + czc - 1) / czc);
             const FastDiv div_nq{sm.qdiv[2 * chi], sm.qdiv[2 * chi + 1]};
-            uint32_t *qn = sm.qn + (ph & 1);
             for (int tau = tid; tau < ntasks; tau += nthr) {
                 const int r = (int)fdiv((uint32_t)tau, div_wc), w = tau - r * wc;
                 const int ch = (int)fdiv((uint32_t)r, div_nq), q = r - ch * nq;
@@ -1086,28 +1182,75 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 tk.valid = valid_bits(J.R, tk.gw);
                 tk.lut = sm.lut + (uint32_t)si * kLutSlot;
                 tk.swz = lut_swizzle(si);
+                tk.ph0 = sm.ph[2 * w];
+                tk.ph1 = sm.ph[2 * w + 1];
                 if (FOLD) {
-                    const int nt = sr.nterm;
+                    const uint4 rb = sm.rec[2 * si + 1];
+                    const uint32_t pp[3] = {rb.x, rb.y, rb.z};
 #pragma unroll
                     for (int k = 0; k < kMaxTerms; k++)
-                        tk.nb[k] = k < nt ? 4u * (uint32_t)(sr.t[k].p[0] * wc + w) : tk.own;
+                        tk.nb[k] = 4u * ((uint32_t)(pp[k >> 1] >> (16 * (k & 1)) & 0xFFFFu) * (uint32_t)wc + (uint32_t)w);
                 }
                 const int zlo = ch * czc, zhi = min(zn, zlo + czc);
-                for (int zz = zlo; zz < zhi; zz++) {
-                    const int zl = KIND == SQA_KIND_SQA ? 2 * zz + par : zz;
-                    const uint32_t tm = metro_item<KIND, LUT, PAIRS>(J, K, sm, pt, tk, sr, inst, t, zl);
-                    queue_ties(J, sm, tk, zl, tm, qn);
-                }
+                const int dz = KIND == SQA_KIND_SQA ? 2 : 1, zl0 = KIND == SQA_KIND_SQA ? 2 * zlo + par : zlo;
+                uint32_t tm[kTaskSlices];
+#pragma unroll
+                for (int i = 0; i < kTaskSlices; i++)
+                    tm[i] = zlo + i < zhi ? metro_item<KIND, LUT, PAIRS>(J, ps, sm, pt, tk, sr, zl0 + i * dz) : 0u;
+                store_task_ties(sm, tau, czc, tm);
             }
-            __syncthreads();  // the phase's queue is complete
-            const uint32_t nties = *qn;
-            if (tid == 0) sm.qn[(ph + 1) & 1] = 0u;  // the next phase's counter (last read a phase ago)
-            for (uint32_t e = tid; e < nties; e += nthr) {
-                const uint2 en = sm.q[e];
-                const uint32_t zl = fdiv(en.x, div_zs), rem = en.x - zl * (uint32_t)J.zstride;
-                const uint32_t si = fdiv(rem, div_wc);
-                resolve_ties<KIND, LUT, PAIRS>(J, sm, pt, inst, w0, wc, t, (int)si, (int)zl, (int)(rem - si * (uint32_t)wc),
-                                               en.y);
+            __syncthreads();  // the phase's tie array is complete
+            {
+                LoKeys lk;
+#pragma unroll
+                for (int r = 0; r < 10; r++) {
+                    lk.a[r] = J.rk0[r];
+                    lk.b[r] = J.rk_lo[r];
+                }
+                // the item of tie-array word p: task p / czc, slice or slot p % czc
+                const auto resolve_at = [&](uint32_t p, uint32_t tmv) -> uint32_t {
+                    const uint32_t tau = czc == 4 ? p >> 2 : czc == 2 ? p >> 1 : czc == 1 ? p : __umulhi(p, 0xAAAAAAABu) >> 1;
+                    const uint32_t i = p - tau * (uint32_t)czc;
+                    const uint32_t r = fdiv(tau, div_wc), w = tau - r * (uint32_t)wc;
+                    const uint32_t ch = fdiv(r, div_nq), q = r - ch * (uint32_t)nq;
+                    const int zz = (int)(ch * (uint32_t)czc + i);
+                    const int zl = KIND == SQA_KIND_SQA ? 2 * zz + par : zz;
+                    return resolve_ties<KIND, LUT, PAIRS, false>(J, sm, pt, lk, inst, w0, wc, t, c0 + (int)q, zl, (int)w,
+                                                                 tmv);
+                };
+                // each warp scans its share of the array, gathers the tied
+                // items on its list and resolves one tie of 32 of them at a
+                // time (every lane busy); items with ties left go back on
+                // the list.  The list holds 63 entries at most: fewer than
+                // 32 before a scan step adds at most 32, and a round takes
+                // 32 off before it puts at most 32 back.
+                const uint32_t lt = (1u << lane) - 1u;
+                const auto round = [&](uint32_t nl) -> uint32_t {
+                    __syncwarp();
+                    const bool mine = (uint32_t)lane < nl, tail = 32u + (uint32_t)lane < nl;
+                    const uint2 en = mine ? rq[lane] : make_uint2(0u, 0u);
+                    const uint2 tl = tail ? rq[32 + lane] : make_uint2(0u, 0u);
+                    __syncwarp();
+                    if (tail) rq[lane] = tl;
+                    const uint32_t m = nl > 32u ? nl - 32u : 0u;
+                    const uint32_t left = mine ? resolve_at(en.x, en.y) : 0u;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, left != 0u);
+                    __syncwarp();
+                    if (left) rq[m + (uint32_t)__popc(bal & lt)] = make_uint2(en.x, left);
+                    return m + (uint32_t)__popc(bal);
+                };
+                const uint32_t npos = (uint32_t)(ntasks * czc);
+                uint32_t nl = 0u;
+                for (uint32_t base = (uint32_t)(tid - lane); base < npos; base += (uint32_t)nthr) {
+                    const uint32_t p = base + (uint32_t)lane;
+                    const uint32_t tmv = p < npos ? sm.tq[p] : 0u;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, tmv != 0u);
+                    __syncwarp();
+                    if (tmv) rq[nl + (uint32_t)__popc(bal & lt)] = make_uint2(p, tmv);
+                    nl += (uint32_t)__popc(bal);
+                    if (nl >= 32u) nl = round(nl);
+                }
+                while (nl > 0u) nl = round(nl);
             }
             if (KIND == SQA_KIND_SQA)
                 cluster_barrier(pt.C);  // neighbouring blocks read this phase's boundary slices

@@ -28,10 +28,19 @@ struct SmemOffsets {
     size_t E;      // PT: energies [P][wc*32]
     size_t M;      // PT: swap masks [P/2+1][wc]; cluster moves: per-warp start masks [8][64 or 128]
     size_t Q;      // 64 bytes: two tie-queue counters, and per colour the divisor of the task decode
+    size_t P;      // single-spin sweep: per word of the unit and SWEEP_HI block, the sweep's
+                   // slice-independent Philox values {P0, Q2, O3, 0} (4 words)
+    size_t R;      // single-spin sweep: per site, the tie record (kTieRec bytes)
+    size_t RQ;     // single-spin sweep: per warp, kRequeue tie-queue entries (uint2)
     size_t total;
 };
 
 SQA_LHD size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+constexpr int kTieRec = 32;     // per-site tie record: threshold-index base and weights, neighbours
+constexpr int kRequeue = 64;    // per-warp list of tied items of a tie pass
+constexpr int kTaskSlices = 4;  // slices (SQA: slice pairs) or slots per task of the single-spin sweep
+constexpr int kMaxWarps = 12;   // warps per block (384 threads) the layout provides for
 
 // Items of one colour phase of a block (SQA: colour x slice parity; PT:
 // colour), at most: every one of them may tie (two equal 7-bit high parts,
@@ -53,7 +62,7 @@ SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
     if (J.kind == SQA_KIND_SQA && J.move == SQA_MOVE_WOLFF) {
         // cluster moves: the state, the site records and, per warp, the
         // start masks of one ring (M): no threshold rows, tables or queue
-        o.T = o.Tb = o.lut = o.Q = off;
+        o.T = o.Tb = o.lut = o.Q = o.P = o.R = o.RQ = off;
         off = align16(off);
         o.sites = off;
         off += (size_t)J.n * sizeof(SiteRec);
@@ -86,6 +95,12 @@ SQA_LHD SmemOffsets smem_layout(const JobDev &J, int wc, int zstride)
     off = align16(off);
     o.Q = off;
     off += 64;
+    o.P = off;
+    off += (size_t)wc * 2 * 16;
+    o.R = off;
+    off += (size_t)J.n * kTieRec;
+    o.RQ = off;
+    off += (size_t)kMaxWarps * kRequeue * 8;
     o.total = align16(off);
     return o;
 }
