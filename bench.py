@@ -86,18 +86,22 @@ def kernels_code_sha256(path):
     return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()
 
 
-def kernel_traffic(n_instances):
-    """DRAM bytes of one sweep launch from the committed ncu capture of the
-    sweep kernel (read + write, per instance, scaled to n_instances), or None
-    when the code of kernels.cu changed since that capture."""
+def kernel_capture(n_instances):
+    """The committed ncu capture of the sweep kernel: DRAM bytes of one launch
+    (read + write per instance, scaled to n_instances) and the kernel's own
+    instruction counters (warp instructions x 32 per attempt, issue-active
+    fraction, pipe utilisation).  None when the code of kernels.cu changed
+    since that capture."""
     p = os.path.join(ROOT, "profiles", "sweep_kernel_traffic.json")
     src = os.path.join(ROOT, "paper_1603_03755_gb300", "csrc", "kernels.cu")
     if not os.path.exists(p):
-        return None, "no capture"
+        return None, "no capture", None
     rec = json.load(open(p))
     if rec.get("kernels_cu_code_sha256") != kernels_code_sha256(src):
-        return None, "kernel changed since the capture"
-    return rec["dram_bytes_per_instance"] * n_instances, rec["note"]
+        return None, "kernel changed since the capture", None
+    counters = {k: rec.get(k) for k in ("instr_per_attempt", "issue_active", "pipe_alu", "pipe_fmaheavy",
+                                        "shared_bank_conflicts_per_wavefront")}
+    return rec["dram_bytes_per_instance"] * n_instances, rec["note"], counters
 
 
 def load_peaks():
@@ -632,7 +636,7 @@ def main():
     intpeak = {k: round(pkg.int_peak(k), 2) for k in pkg.INT_PEAK_KINDS}
     t_sweep = statistics.mean(sweep_times)
     achieved_gops = attempts * OPS_PER_ATTEMPT / t_sweep / 1e9
-    traffic, traffic_note = kernel_traffic(I)
+    traffic, traffic_note, counters = kernel_capture(I)
     extra = None if args.no_extra else extra_workloads(pkg, stream, args)
     cpu = None
     if not args.no_cpu_baseline:
@@ -640,6 +644,19 @@ def main():
         rate, cores, desc = cpu_oracle_all_cores(cfg, 10.0)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                "single_thread": {"value": rate1, "sample": desc1}}
+    mixed = intpeak["lop3_imad"]                         # lane-ops / SM clock, ALU and FMA pipes interleaved
+    mixed_gops = n_sm * f_mhz * 1e6 * mixed / 1e9
+    ipa = (counters or {}).get("instr_per_attempt")
+    per_inst = {"value": per_inst_rate, "unit": UNIT, "instances_sampled": ns,
+                "same_bits_as_batched": bool(same), "batched_over_per_instance": value / world / per_inst_rate}
+    rates = None
+    if extra:
+        rates = {k: extra[k]["value"] for k in ("ragged_mix", "pt_me", "pt_lhz") if k in extra}
+        if "wolff_me" in extra:
+            rates["wolff_me_spin_slice_updates"] = extra["wolff_me"]["value"]
+        if "serving_capacity" in extra:
+            rates["serving_capacity"] = extra["serving_capacity"]["attempts_per_s"]
+        rates["unit"] = UNIT
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
@@ -647,27 +664,37 @@ def main():
         "config": {"workload": cfg["name"], "embedding": "me_chimera_2x2", "N": N, "instances": I,
                    "replicas": R, "slices": L, "sweeps": S, "parallelism": "replicas",
                    "l2": "flushed between steps (256 MiB write)"},
+        "per_instance_path": per_inst,
+        "workload_rates": rates,
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved_gops / peak_gops, "traffic": traffic, "traffic_note": traffic_note,
                      "kernel": "sweep_kernel", "ops_per_attempt": OPS_PER_ATTEMPT,
                      "peak_basis": f"{n_sm} SMs x 4 SMSP x 32 lanes x {f_mhz:.0f} MHz (median SM clock under load)",
+                     "instr_per_attempt": ipa,
+                     "issue_active": (counters or {}).get("issue_active"),
+                     "pipes": None if not counters else {"alu": counters.get("pipe_alu"),
+                                                         "fmaheavy": counters.get("pipe_fmaheavy")},
+                     "counters_source": "ncu capture of the sweep kernel (profiles/sweep_kernel_traffic.json)"
+                                        if counters else traffic_note,
+                     "mixed_pipe_ceiling": {
+                         "lane_ops_per_sm_clk": mixed, "gops": mixed_gops,
+                         "frac": achieved_gops / mixed_gops,
+                         "attempts_per_s_at_kernel_instr": (n_sm * f_mhz * 1e6 * mixed / ipa) if ipa else None,
+                         "basis": "measured LOP3/IMAD interleaved issue rate x SMs x median SM clock"},
                      "sweep_kernel_s": t_sweep,
                      "measured_lane_ops_per_sm_clk": intpeak},
-        "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "cpu_baseline": cpu,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
-        "per_instance_path": {"value": per_inst_rate, "unit": UNIT, "instances_sampled": ns,
-                              "same_bits_as_batched": bool(same),
-                              "batched_over_per_instance": value / world / per_inst_rate},
-        "peaks_source": src,
-        "other_workloads": extra,
         "latency": None if not extra or "serving" not in extra else dict(
             {f"load_{int(100 * x['offered_load'])}pct": {"p50_s": x["p50_latency_s"], "p99_s": x["p99_latency_s"]}
              for x in extra["serving"]},
             loads_relative_to={"attempts_per_s": extra["serving_capacity"]["attempts_per_s"],
                                "basis": extra["serving_capacity"]["basis"]}),
         "launch": dict(h.launch(), autotune_trial_attempts_per_s=tuned["trial_attempts_per_s"]),
+        "peaks_source": src,
+        "other_workloads": extra,
     }
     print(json.dumps(out))
     barrier(dist)

@@ -55,7 +55,8 @@ typedef enum {
     SQA_ERR_CUDA = -4,        /* a CUDA call failed; see sqa_last_error() */
     SQA_ERR_TIMEOUT = -5,     /* a bounded wait ran out */
     SQA_ERR_NO_DEVICE = -6,   /* no CUDA device is visible */
-    SQA_ERR_BUSY = -7         /* resource in use (server full, job pending) */
+    SQA_ERR_BUSY = -7,        /* resource in use (server full, job pending) */
+    SQA_ERR_BOUNDS = -8       /* a bounds-checked build recorded an out-of-range access */
 } sqa_status;
 
 typedef enum { SQA_EMB_ME_CHIMERA = 0, SQA_EMB_LHZ = 1 } sqa_embedding;
@@ -370,6 +371,26 @@ sqa_status sqa_plan_tree(int32_t N, uint64_t seed, int32_t inst, int32_t tree, i
  * blocks (result in blocks, not instructions), 7 the same with one
  * 32x32->64 multiply per product.  Synchronous. */
 sqa_status sqa_int_peak(int32_t kind, double *lane_ops_per_clk_per_sm);
+
+/* Bounds-checked builds (no paper counterpart; a debugging aid).  A build
+ * compiled with -DSQA_BOUNDS_CHECK tests, before each access of the sweep,
+ * energy and decode kernels, every shared-memory address against the
+ * block's dynamic window and every state, threshold-row, tie-array,
+ * tie-list, PT swap and cluster-move ring index against its buffer.  An
+ * access out of range is skipped (a load reads 0) and recorded in a device
+ * status word; no kernel traps, so the context stays usable.
+ * sqa_bounds_checked() returns 1 in such a build, 0 otherwise.
+ * sqa_check_status() synchronises the device, copies the record into
+ * record[4] and clears it: record[0] = violations since the last call,
+ * record[1] = the check site of the first (1 shared memory, 2 state word,
+ * 3 threshold row, 4 tie array, 5 tie list, 6 decoded tie item, 7 a
+ * neighbouring block's slice, 8 PT swap, 9 cluster-move ring), record[2] =
+ * its index (for shared memory: its shared-window byte address),
+ * record[3] = the bound it broke.  Returns SQA_OK when nothing was
+ * recorded, SQA_ERR_BOUNDS otherwise (detail in sqa_last_error()); in an
+ * unchecked build SQA_OK with a zero record.  record NULL -> SQA_ERR_INVALID. */
+int32_t sqa_bounds_checked(void);
+sqa_status sqa_check_status(uint32_t record[4]);
 
 const char *sqa_strerror(sqa_status s);
 /* Detail of the last error on this thread (CUDA message, bad field). */

@@ -18,12 +18,15 @@ from . import build as _build
 
 SQA_OK, SQA_ERR_INVALID, SQA_ERR_UNSUPPORTED, SQA_ERR_NOMEM = 0, -1, -2, -3
 SQA_ERR_CUDA, SQA_ERR_TIMEOUT, SQA_ERR_NO_DEVICE, SQA_ERR_BUSY = -4, -5, -6, -7
+SQA_ERR_BOUNDS = -8
 EMB = {"me": 0, "lhz": 1}
 KIND = {"sqa": 0, "pt": 1}
 MOVE = {"metropolis": 0, "wolff": 1}
 DECODE = {"me_mv": 0, "lhz_trees": 1, "lhz_star": 2, "lhz_chain": 3, "lhz_mwd": 4, "lhz_bp": 5}
 
-LIB_PATH = _build.LIB
+# SQA_GB300_CHECKED=1 loads the bounds-checked build (see build.build(checked=True))
+CHECKED = os.environ.get("SQA_GB300_CHECKED", "") == "1"
+LIB_PATH = _build.LIB_CHECKED if CHECKED else _build.LIB
 
 
 class SQAError(RuntimeError):
@@ -86,6 +89,8 @@ _SIGS = {
                                         C.c_int64, C.POINTER(C.c_int64)]),
     "sqa_plan_tree": (C.c_int, [C.c_int32, C.c_uint64, C.c_int32, C.c_int32, C.c_void_p]),
     "sqa_int_peak": (C.c_int, [C.c_int32, C.POINTER(C.c_double)]),
+    "sqa_bounds_checked": (C.c_int32, []),
+    "sqa_check_status": (C.c_int, [C.POINTER(C.c_uint32)]),
     "sqa_server_create": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_void_p)]),
     "sqa_server_submit": (C.c_int, [C.c_void_p, C.POINTER(_Desc), C.POINTER(C.c_uint64)]),
     "sqa_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
@@ -107,7 +112,8 @@ def lib() -> C.CDLL:
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1603_03755_gb300.build.build()")
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1603_03755_gb300.build.build("
+                              f"{'checked=True' if CHECKED else ''})")
         L = C.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
             f = getattr(L, name)
@@ -423,6 +429,15 @@ def ground_energy(N: int, J) -> np.ndarray:
 
 INT_PEAK_KINDS = ("lop3", "iadd3", "imad", "imad_wide", "imad_hi", "lop3_imad", "philox_blocks",
                   "philox_wide_blocks")
+
+
+def check_status() -> tuple[int, list[int]]:
+    """Status and record of the bounds checks since the last call (a
+    bounds-checked build; an unchecked one returns SQA_OK and zeros):
+    [violations, check site, index, bound]."""
+    rec = (C.c_uint32 * 4)()
+    st = lib().sqa_check_status(rec)
+    return st, list(rec)
 
 
 def int_peak(kind: str) -> float:

@@ -196,6 +196,7 @@ extern "C" {
 
 sqa_status sqa_batch_create(sqa_handle *const *hs, int32_t n, sqa_batch **out)
 {
+    NvtxScope nvtx_("sqa_batch_create");
     if (!hs || n < 1 || !out) return set_error("batch arguments"), SQA_ERR_INVALID;
     *out = nullptr;
     for (int k = 0; k < n; k++) {
@@ -217,6 +218,7 @@ sqa_status sqa_batch_create(sqa_handle *const *hs, int32_t n, sqa_batch **out)
 
 sqa_status sqa_batch_launch(sqa_batch *b, void *stream)
 {
+    NvtxScope nvtx_("sqa_batch_launch");
     if (!b) return set_error("NULL batch"), SQA_ERR_INVALID;
     if (!b->exec) {
         const sqa_status st = build_graph(b);
@@ -229,6 +231,7 @@ sqa_status sqa_batch_launch(sqa_batch *b, void *stream)
 sqa_status sqa_batch_autotune(sqa_batch *b, int32_t n_trial, void *stream, int32_t *words_per_unit,
                               double *attempts_per_s)
 {
+    NvtxScope nvtx_("sqa_batch_autotune");
     if (!b || n_trial < 1) return set_error("autotune arguments"), SQA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     int wmax = 1;
@@ -276,6 +279,7 @@ void sqa_batch_destroy(sqa_batch *b)
 sqa_status sqa_autotune(sqa_handle *h, int32_t n_trial, void *stream, int32_t *words_per_unit,
                         int32_t *use_table, int32_t *cluster, double *attempts_per_s)
 {
+    NvtxScope nvtx_("sqa_autotune");
     const sqa_status us = usable(h);
     if (us != SQA_OK) return us;
     if (n_trial < 1) return set_error("autotune arguments"), SQA_ERR_INVALID;

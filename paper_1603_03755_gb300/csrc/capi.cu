@@ -645,6 +645,7 @@ const char *sqa_strerror(sqa_status s)
     case SQA_ERR_TIMEOUT: return "timeout";
     case SQA_ERR_NO_DEVICE: return "no CUDA device";
     case SQA_ERR_BUSY: return "busy";
+    case SQA_ERR_BOUNDS: return "bounds check";
     }
     return "unknown status";
 }
@@ -653,6 +654,7 @@ const char *sqa_last_error(void) { return g_err.c_str(); }
 
 sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
 {
+    NvtxScope nvtx_("sqa_create");
     if (!out) return set_error("out is NULL"), SQA_ERR_INVALID;
     *out = nullptr;
     sqa_status st = validate(d);
@@ -808,6 +810,7 @@ sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t 
 
 sqa_status sqa_run_sweeps(sqa_handle *h, int32_t t0, int32_t t1, void *stream)
 {
+    NvtxScope nvtx_("sqa_run_sweeps");
     sqa_status us = usable(h);
     if (us != SQA_OK) return us;
     if (t0 < 0 || t1 < t0 || t1 > h->S) return set_error("sweep range"), SQA_ERR_INVALID;
@@ -826,6 +829,7 @@ sqa_status sqa_run(sqa_handle *h, void *stream)
 
 sqa_status sqa_run_per_instance(sqa_handle *h, void *stream)
 {
+    NvtxScope nvtx_("sqa_run_per_instance");
     sqa_status us = usable(h);
     if (us != SQA_OK) return us;
     cudaStream_t s = (cudaStream_t)stream;
@@ -844,6 +848,7 @@ sqa_status sqa_run_per_instance(sqa_handle *h, void *stream)
 sqa_status pt_run(sqa_handle *h, const double *betas, int32_t n_temps, int32_t n_sweeps,
                   int32_t swap_every, void *stream)
 {
+    NvtxScope nvtx_("pt_run");
     if (!h || !betas || n_temps < 1 || n_sweeps < 1 || swap_every < 1)
         return set_error("pt_run arguments"), SQA_ERR_INVALID;
     for (int p = 0; p < n_temps; p++)
@@ -864,6 +869,7 @@ sqa_status pt_run(sqa_handle *h, const double *betas, int32_t n_temps, int32_t n
 
 sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
 {
+    NvtxScope nvtx_("sqa_batch_run");
     if (!hs || n < 1) return set_error("batch arguments"), SQA_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<JobDev> jobs;
@@ -962,6 +968,7 @@ static sqa_status canon_out(sqa_handle *h, int z0, int zc, uint32_t *out, int ou
 
 sqa_status sqa_readout(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *stream)
 {
+    NvtxScope nvtx_("sqa_readout");
     return canon_out(h, 0, 1, out, out_is_device, stream);
 }
 
@@ -973,6 +980,7 @@ sqa_status sqa_state(sqa_handle *h, uint32_t *out, int32_t out_is_device, void *
 
 sqa_status sqa_energies(sqa_handle *h, int32_t *out, int32_t out_is_device, void *stream)
 {
+    NvtxScope nvtx_("sqa_energies");
     sqa_status us = usable(h);
     if (us != SQA_OK) return us;
     if (!out) return set_error("NULL argument"), SQA_ERR_INVALID;
@@ -1021,6 +1029,7 @@ static sqa_status decode_impl(sqa_handle *h, int32_t method, int32_t n_trees, do
                               int8_t *logical_out, int64_t *energy_out, const int64_t *e_ground,
                               int32_t *success_out, int32_t out_is_device, void *stream)
 {
+    NvtxScope nvtx_("sqa_decode");
     const sqa_status us = usable(h);
     if (us != SQA_OK) return us;
     const bool me = h->emb == SQA_EMB_ME_CHIMERA;
@@ -1117,6 +1126,7 @@ static sqa_status decode_impl(sqa_handle *h, int32_t method, int32_t n_trees, do
 
 sqa_status sqa_ground_energy(int32_t N, int32_t n_instances, const int32_t *J, int64_t *e_out)
 {
+    NvtxScope nvtx_("sqa_ground_energy");
     if (N < 2 || N > 40 || n_instances < 1 || !J || !e_out) return set_error("ground arguments"), SQA_ERR_INVALID;
     // a bound on the search's work: one call enumerates at most 2^40 states
     // in all (a few seconds), so no call can hold the device for hours

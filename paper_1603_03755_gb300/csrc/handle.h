@@ -2,11 +2,22 @@
 // points shared by the C ABI (capi.cu) and the serving loop (server.cu).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
 
 #include "sqa_internal.h"
+
+// A named NVTX range over a scope, so that a profiler's host timeline shows
+// the library's calls (create, run, decode, batch launches, serving chunks);
+// with no profiler attached a push and a pop cost a few nanoseconds.
+struct NvtxScope {
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 struct sqa_handle {
     // copied description

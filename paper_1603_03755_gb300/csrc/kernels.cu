@@ -33,11 +33,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
+#include "check.cuh"
 #include "layout.cuh"
+#include "handle.h"
 #include "philox.cuh"
 #include "sqa_internal.h"
 
 namespace sqa {
+
 
 __device__ __forceinline__ uint32_t valid_bits(int R, int gw)
 {
@@ -93,6 +98,7 @@ struct Smem {
     uint32_t *qn;     // tie queue counters (two, used by alternate phases)
     uint32_t *qdiv;   // per colour: the task decode's divisor {m, sh} (FastDiv)
     uint32_t *tq;     // this block's tie array: one tie mask per item of a phase (global memory)
+    uint32_t tq_words;  // its length in words
     uint4 *ph;        // per word of the unit and SWEEP_HI block: the sweep's hoisted Philox values
     uint4 *rec;       // per site: the tie record (two uint4)
     uint2 *rq;        // per warp: kRequeue entries of items with ties left after a tie pass
@@ -114,6 +120,7 @@ __device__ __forceinline__ Smem carve(const JobDev &J, unsigned char *base)
     m.qn = (uint32_t *)(base + o.Q);
     m.qdiv = (uint32_t *)(base + o.Q + 16);
     m.tq = (uint32_t *)(J.tieq + (size_t)blockIdx.x * (size_t)J.tieq_stride);
+    m.tq_words = 2u * (uint32_t)J.tieq_stride;
     m.ph = (uint4 *)(base + o.P);
     m.rec = (uint4 *)(base + o.R);
     m.rq = (uint2 *)(base + o.RQ);
@@ -163,26 +170,26 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t x, FastDiv f) { return f.m == 
 // Shared memory by 32-bit shared-window address (the sweep's hot loads).
 __device__ __forceinline__ uint32_t lds32(uint32_t a)
 {
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    uint32_t v = 0u;
+    if (SQA_SHARED_OK(a, 4u)) asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 
 __device__ __forceinline__ uint32_t lds8(uint32_t a)
 {
-    uint32_t v;
-    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
+    uint32_t v = 0u;
+    if (SQA_SHARED_OK(a, 1u)) asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(a));
     return v;
 }
 
 __device__ __forceinline__ void sts32(uint32_t a, uint32_t v)
 {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+    if (SQA_SHARED_OK(a, 4u)) asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void sts8(uint32_t a, uint32_t v)
 {
-    asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+    if (SQA_SHARED_OK(a, 1u)) asm volatile("st.shared.u8 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
 // Term planes of one item: bit b of pl[k] is set when term k's value is
@@ -427,11 +434,11 @@ __device__ __forceinline__ void item_planes(const JobDev &J, const Smem &sm, con
             if (zl > 0)
                 up = lds32(row - zs4 + tk.own);
             else
-                up = pt.up[tk.own >> 2];
+                up = SQA_IN(kChkNeighbour, tk.own >> 2, J.zstride) ? pt.up[tk.own >> 2] : 0u;
             if (zl < pt.zr - 1)
                 dn = lds32(row + zs4 + tk.own);
             else
-                dn = pt.dn[tk.own >> 2];
+                dn = SQA_IN(kChkNeighbour, tk.own >> 2, J.zstride) ? pt.dn[tk.own >> 2] : 0u;
         }
         d1 = s ^ up;
         d2 = s ^ dn;
@@ -512,7 +519,7 @@ __device__ __forceinline__ uint32_t resolve_ties(const JobDev &J, const Smem &sm
 #pragma unroll
         for (int k = 0; k < kMaxTerms; k++)
             U += (int)((pl[k] >> b) & 1u) * (int)(int16_t)(swp[k >> 1] >> (16 * (k & 1)));
-        const uint32_t T = Trow[U];
+        const uint32_t T = SQA_IN(kChkThreshold, U, J.nrow) ? Trow[U] : 0u;
         const uint32_t rho = gw * 32u + (uint32_t)b;
         const U4 B = philox_rk((uint32_t)t, slot, rho >> 2, (uint32_t)inst, lk.a, lk.b);
         const uint32_t r = rho & 3u;
@@ -578,7 +585,7 @@ __device__ __forceinline__ void store_task_ties(const Smem &sm, int tau, int czc
     uint32_t *a = sm.tq + (size_t)tau * czc;
 #pragma unroll
     for (int i = 0; i < kTaskSlices; i++)
-        if (i < czc) a[i] = tm[i];
+        if (i < czc && SQA_IN(kChkTieArray, (size_t)tau * czc + i, sm.tq_words)) a[i] = tm[i];
 }
 
 // Where a site's table keeps the entry of code c: at byte c ^ swz of its
@@ -619,7 +626,7 @@ __device__ void build_luts(const JobDev &J, const Smem &sm)
 #pragma unroll
             for (int k = 0; k < kMaxTerms; k++)
                 if ((((uint32_t)c >> (k + 2)) & 1u) ^ flip[k]) U += aw[k];
-            sts8(slot + ((uint32_t)c ^ swz), sm.T[base + U] >> 25);
+            sts8(slot + ((uint32_t)c ^ swz), SQA_IN(kChkThreshold, base + U, J.nrow) ? sm.T[base + U] >> 25 : 0u);
         }
     }
 }
@@ -790,16 +797,18 @@ __device__ void pt_swap(const JobDev &J, const Smem &sm, const Part &pt, int ins
         const int p = first + 2 * k, pl = p - z0;
         const int gw = w0 + w;
         const int rho = gw * 32 + b;
-        const int32_t Eu = pl + 1 < zr ? sm.E[((pl + 1) * wc + w) * 32 + b] : E_next[(0 * wc + w) * 32 + b];
-        const int dE = Eu - sm.E[(pl * wc + w) * 32 + b];
-        bool accept = dE <= 0;
-        if (!accept && dE <= J.sw_len[p]) {
+        // (the ballot below stays convergent: a failed check only clears accept)
+        const bool ok = SQA_IN(kChkSwap, pl, zr);
+        const int32_t Eu = !ok ? 0 : pl + 1 < zr ? sm.E[((pl + 1) * wc + w) * 32 + b] : E_next[(0 * wc + w) * 32 + b];
+        const int dE = !ok ? 0 : Eu - sm.E[(pl * wc + w) * 32 + b];
+        bool accept = ok && dE <= 0;
+        if (ok && !accept && dE <= J.sw_len[p]) {
             const U4 v = philox((uint32_t)e, (uint32_t)p, (uint32_t)(rho >> 2), (uint32_t)inst, J.seed_lo,
                                 J.key_swap);
             accept = word_of(v, rho & 3) < J.Tsw[J.sw_off[p] + dE - 1];
         }
         const uint32_t M = __ballot_sync(0xFFFFFFFFu, accept) & valid_bits(J.R, gw);
-        if (b == 0) sm.M[k * wc + w] = M;
+        if (b == 0 && SQA_IN(kChkSwap, k * wc + w, (zr / 2 + 1) * wc)) sm.M[k * wc + w] = M;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < npairs * n * wc; it += nthr) {
@@ -807,6 +816,7 @@ __device__ void pt_swap(const JobDev &J, const Smem &sm, const Part &pt, int ins
         const int pl = first + 2 * k - z0;
         uint32_t *a = sm.S + (size_t)pl * J.zstride + si * wc + w;
         uint32_t *c = pl + 1 < zr ? sm.S + (size_t)(pl + 1) * J.zstride + si * wc + w : S_next + si * wc + w;
+        if (!(SQA_IN(kChkSwap, k * wc + w, (zr / 2 + 1) * wc) && SQA_IN(kChkSwap, pl, zr))) continue;
         const uint32_t va = *a, vc = *c;
         const uint32_t d = (va ^ vc) & sm.M[k * wc + w];
         *a = va ^ d;
@@ -878,7 +888,7 @@ __device__ __forceinline__ void wolff_item(const JobDev &J, const Smem &sm, uint
         const int tau = lane * SPL + j;
         s[j] = 0u;
         A[j] = 0u;
-        if (tau < L) {
+        if (tau < L && SQA_IN(kChkRing, (size_t)tau * J.zstride + idx, (size_t)L * J.zstride)) {
             s[j] = sm.S[(size_t)tau * J.zstride + idx];
             const uint32_t nx = sm.S[(size_t)(tau + 1 == L ? 0 : tau + 1) * J.zstride + idx];
             const uint32_t eq = ~(s[j] ^ nx);
@@ -1019,7 +1029,8 @@ __device__ __forceinline__ void wolff_item(const JobDev &J, const Smem &sm, uint
 #pragma unroll
     for (int j = 0; j < SPL; j++) {
         const int tau = lane * SPL + j;
-        if (tau < L) sm.S[(size_t)tau * J.zstride + idx] = s[j] ^ (C[j] & flip);
+        if (tau < L && SQA_IN(kChkRing, (size_t)tau * J.zstride + idx, (size_t)L * J.zstride))
+            sm.S[(size_t)tau * J.zstride + idx] = s[j] ^ (C[j] & flip);
     }
 }
 
@@ -1030,9 +1041,11 @@ __device__ void run_unit_wolff(const JobDev &J, const Smem &sm, const Unit &u)
 {
     const int nthr = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
     const int Z = J.Z, n = J.n, wc = u.wc, inst = u.inst, w0 = u.w0;
+    const size_t n_state = (size_t)J.n_inst * Z * n * J.W;
     for (int i = tid; i < Z * n * wc; i += nthr) {
         const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
-        sm.S[(size_t)zl * J.zstride + si * wc + w] = J.state[(((size_t)inst * Z + zl) * n + si) * J.W + w0 + w];
+        const size_t g = (((size_t)inst * Z + zl) * n + si) * J.W + w0 + w;
+        sm.S[(size_t)zl * J.zstride + si * wc + w] = SQA_IN(kChkState, g, n_state) ? J.state[g] : 0u;
     }
     for (int i = tid; i < Z * wc; i += nthr) sm.S[(size_t)(i / wc) * J.zstride + n * wc + i % wc] = 0u;
     {
@@ -1055,7 +1068,8 @@ __device__ void run_unit_wolff(const JobDev &J, const Smem &sm, const Unit &u)
     }
     for (int i = tid; i < Z * n * wc; i += nthr) {
         const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
-        J.state[(((size_t)inst * Z + zl) * n + si) * J.W + w0 + w] = sm.S[(size_t)zl * J.zstride + si * wc + w];
+        const size_t g = (((size_t)inst * Z + zl) * n + si) * J.W + w0 + w;
+        if (SQA_IN(kChkState, g, n_state)) J.state[g] = sm.S[(size_t)zl * J.zstride + si * wc + w];
     }
     __syncthreads();
 }
@@ -1101,10 +1115,11 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
     pt.z0 = pt.rank * pt.zr;
     const int zr = pt.zr, z0 = pt.z0;
     // stage this block's slices (and each row's zero slot) and the site records
+    const size_t n_state = (size_t)J.n_inst * Z * n * J.W;
     for (int i = tid; i < zr * n * wc; i += nthr) {
         const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
-        sm.S[(size_t)zl * J.zstride + si * wc + w] =
-            J.state[(((size_t)inst * Z + z0 + zl) * n + si) * J.W + w0 + w];
+        const size_t g = (((size_t)inst * Z + z0 + zl) * n + si) * J.W + w0 + w;
+        sm.S[(size_t)zl * J.zstride + si * wc + w] = SQA_IN(kChkState, g, n_state) ? J.state[g] : 0u;
     }
     for (int i = tid; i < zr * wc; i += nthr) sm.S[(size_t)(i / wc) * J.zstride + n * wc + i % wc] = 0u;
     {
@@ -1215,6 +1230,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                     const uint32_t ch = fdiv(r, div_nq), q = r - ch * (uint32_t)nq;
                     const int zz = (int)(ch * (uint32_t)czc + i);
                     const int zl = KIND == SQA_KIND_SQA ? 2 * zz + par : zz;
+                    if (!(SQA_IN(kChkItem, q, nq) && SQA_IN(kChkItem, zl, zr) && SQA_IN(kChkItem, w, wc))) return 0u;
                     return resolve_ties<KIND, LUT, PAIRS, false>(J, sm, pt, lk, inst, w0, wc, t, c0 + (int)q, zl, (int)w,
                                                                  tmv);
                 };
@@ -1229,24 +1245,27 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                     __syncwarp();
                     const bool mine = (uint32_t)lane < nl, tail = 32u + (uint32_t)lane < nl;
                     const uint2 en = mine ? rq[lane] : make_uint2(0u, 0u);
-                    const uint2 tl = tail ? rq[32 + lane] : make_uint2(0u, 0u);
+                    const uint2 tl = tail && SQA_IN(kChkRequeue, 32 + lane, kRequeue) ? rq[32 + lane]
+                                                                                       : make_uint2(0u, 0u);
                     __syncwarp();
                     if (tail) rq[lane] = tl;
                     const uint32_t m = nl > 32u ? nl - 32u : 0u;
                     const uint32_t left = mine ? resolve_at(en.x, en.y) : 0u;
                     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, left != 0u);
                     __syncwarp();
-                    if (left) rq[m + (uint32_t)__popc(bal & lt)] = make_uint2(en.x, left);
+                    const uint32_t slot = m + (uint32_t)__popc(bal & lt);
+                    if (left && SQA_IN(kChkRequeue, slot, kRequeue)) rq[slot] = make_uint2(en.x, left);
                     return m + (uint32_t)__popc(bal);
                 };
                 const uint32_t npos = (uint32_t)(ntasks * czc);
                 uint32_t nl = 0u;
                 for (uint32_t base = (uint32_t)(tid - lane); base < npos; base += (uint32_t)nthr) {
                     const uint32_t p = base + (uint32_t)lane;
-                    const uint32_t tmv = p < npos ? sm.tq[p] : 0u;
+                    const uint32_t tmv = p < npos && SQA_IN(kChkTieArray, p, sm.tq_words) ? sm.tq[p] : 0u;
                     const uint32_t bal = __ballot_sync(0xFFFFFFFFu, tmv != 0u);
                     __syncwarp();
-                    if (tmv) rq[nl + (uint32_t)__popc(bal & lt)] = make_uint2(p, tmv);
+                    const uint32_t slot = nl + (uint32_t)__popc(bal & lt);
+                    if (tmv && SQA_IN(kChkRequeue, slot, kRequeue)) rq[slot] = make_uint2(p, tmv);
                     nl += (uint32_t)__popc(bal);
                     if (nl >= 32u) nl = round(nl);
                 }
@@ -1262,7 +1281,8 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
     }
     for (int i = tid; i < zr * n * wc; i += nthr) {
         const int w = i % wc, r = i / wc, si = r % n, zl = r / n;
-        J.state[(((size_t)inst * Z + z0 + zl) * n + si) * J.W + w0 + w] = sm.S[(size_t)zl * J.zstride + si * wc + w];
+        const size_t g = (((size_t)inst * Z + z0 + zl) * n + si) * J.W + w0 + w;
+        if (SQA_IN(kChkState, g, n_state)) J.state[g] = sm.S[(size_t)zl * J.zstride + si * wc + w];
     }
     cluster_barrier(pt.C);  // no block restages while another still reads its slices
 }
@@ -1442,7 +1462,8 @@ __global__ void energy_kernel(JobDev J, int32_t *out)
         for (int q = 0; q < J.n_eterms; q++) {
             const ETerm x = et[q];
             uint32_t v = 0u;
-            for (int k = 0; k < x.size; k++) v ^= st[(size_t)x.m[k] * J.W + gw];
+            for (int k = 0; k < x.size; k++)
+                if (SQA_IN(kChkState, x.m[k], J.n)) v ^= st[(size_t)x.m[k] * J.W + gw];
             E += ((v >> b) & 1u) ? -x.w : x.w;
         }
         out[i] = E;
@@ -1478,7 +1499,10 @@ __global__ void decode_kernel(JobDev J, DecodeArgs D)
         const int rho = (int)(i % J.R), inst = (int)(i / J.R);
         const int gw = rho >> 5, b = rho & 31;
         const uint32_t *st = J.state + (size_t)inst * J.Z * J.n * J.W;  // z = 0
-        auto sig = [&](int si) -> int { return ((st[(size_t)si * J.W + gw] >> b) & 1u) ? -1 : 1; };
+        auto sig = [&](int si) -> int {
+            if (!SQA_IN(kChkState, si, J.n)) return 1;
+            return ((st[(size_t)si * J.W + gw] >> b) & 1u) ? -1 : 1;
+        };
         int8_t q[kMaxN];
         if (D.method == SQA_DECODE_ME_MV) {
             const int len = D.Lc + 1;
@@ -1639,3 +1663,36 @@ __global__ void ground_kernel(int N, const int32_t *J, int chunk_bits, int64_t n
 }
 
 }  // namespace sqa
+
+extern "C" {
+
+int32_t sqa_bounds_checked(void)
+{
+#ifdef SQA_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+sqa_status sqa_check_status(uint32_t *record)
+{
+    if (!record) return sqa::set_error("NULL record"), SQA_ERR_INVALID;
+    for (int k = 0; k < 4; k++) record[k] = 0u;
+#ifdef SQA_BOUNDS_CHECK
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(record, sqa::g_check, 4 * sizeof(uint32_t));
+    const uint32_t zero[4] = {0u, 0u, 0u, 0u};
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(sqa::g_check, zero, sizeof(zero));
+    if (e != cudaSuccess) return sqa::cuda_fail(e, "sqa_check_status");
+    if (record[0] != 0u) {
+        sqa::set_error("bounds check: " + std::to_string(record[0]) + " violation(s), first at check site " +
+                       std::to_string(record[1]) + ", index " + std::to_string(record[2]) + " of bound " +
+                       std::to_string(record[3]));
+        return SQA_ERR_BOUNDS;
+    }
+#endif
+    return SQA_OK;
+}
+
+}  // extern "C"

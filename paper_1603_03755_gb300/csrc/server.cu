@@ -94,6 +94,7 @@ void fail_job(sqa_server *s, Job *j, sqa_status st)
 // (the caller counts it in the stats under s->mu).
 sqa_status launch_chunk(sqa_server *s, Job *j)
 {
+    NvtxScope nvtx_("server_chunk");
     sqa_handle *h = j->h;
     JobDev J = h->job;
     const int64_t unit_attempts = (int64_t)J.n * J.zr * J.wc * 32;
@@ -127,6 +128,7 @@ void drop_device(sqa_server *s, Job *j)
 // starts their first chunks.
 void admit(sqa_server *s)
 {
+    NvtxScope nvtx_("server_admit");
     for (;;) {
         Job *j = nullptr;
         {
@@ -328,6 +330,7 @@ sqa_status sqa_server_create(int64_t mem_budget_bytes, int64_t unit_attempts_per
 
 sqa_status sqa_server_submit(sqa_server *s, const sqa_desc *d, uint64_t *job_id)
 {
+    NvtxScope nvtx_("sqa_server_submit");
     if (!s || !d || !job_id) return set_error("submit arguments"), SQA_ERR_INVALID;
     Job *j = new (std::nothrow) Job();
     if (!j) return SQA_ERR_NOMEM;

@@ -232,3 +232,29 @@ def test_no_device_is_reported():
     assert pkg.lib().sqa_create(C.byref(d), C.byref(h)) == pkg.SQA_ERR_NO_DEVICE
     with pytest.raises(pkg.SQAError):
         pkg.Handle(embedding="lhz", N=6, J=J, penalty=9, sweeps=10, R=32)
+
+
+def test_unchecked_build_reports_a_clear_status(L):
+    """The normal build has no bounds checks: sqa_bounds_checked() is 0 and
+    sqa_check_status() answers SQA_OK with a zero record (no device call)."""
+    assert L.sqa_bounds_checked() == 0
+    rec = (C.c_uint32 * 4)(7, 7, 7, 7)
+    assert L.sqa_check_status(rec) == pkg.SQA_OK and list(rec) == [0, 0, 0, 0]
+    assert L.sqa_check_status(None) == pkg.SQA_ERR_INVALID
+    assert L.sqa_strerror(pkg.SQA_ERR_BOUNDS) == b"bounds check"
+
+
+def test_checked_build_compiles_and_exports_every_symbol():
+    """The bounds-checked variant (-DSQA_BOUNDS_CHECK) builds for sm_103a and
+    exports the same ABI; loaded in a child process it reports itself as
+    checked."""
+    import subprocess
+    import sys
+    from paper_1603_03755_gb300 import build as b
+    path = b.build(checked=True)
+    names = _declared()
+    code = ("import ctypes, sys; L = ctypes.CDLL(sys.argv[1]); "
+            "missing = [n for n in sys.argv[2:] if not hasattr(L, n)]; "
+            "assert not missing, missing; assert L.sqa_bounds_checked() == 1; print('ok')")
+    r = subprocess.run([sys.executable, "-c", code, path, *names], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr

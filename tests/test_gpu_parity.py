@@ -4,8 +4,8 @@ Spins, energies, decoded states and success counts are compared bit for bit
 (integer work: the tolerance is zero).  Sizes are small enough for the oracle
 to finish in seconds but span several classes, words and a ragged replica
 tail; the edge cases cover L = 2, one physical spin, a partial Chimera group,
-an infinite Jperp (A = 0), PT with one slot, and a full-size launch checked
-on sampled replicas.
+an infinite Jperp (A = 0) and PT with one slot.  The full-size launches are
+checked on sampled replicas in test_gpu_fullsize.py.
 """
 import numpy as np
 import pytest
@@ -302,26 +302,6 @@ def test_ground_energy_parity(N):
     got = pkg.ground_energy(N, J)
     want = [O.ground_energy(N, J[i])[0] for i in range(4)]
     assert list(got) == want
-
-
-def test_full_size_me_k8_batch_sampled():
-    """The benchmark's workload and launch: ME K_8, 1024 instances x 256
-    replicas, L = 64, 1e4 sweeps, one persistent launch.  Sampled replicas of
-    the first and last instance are re-run by the oracle; every sampled
-    energy is recomputed from the spins."""
-    c = W.me_n8_batch_config()
-    h = pkg.Handle(embedding="me", N=c["N"], J=c["J"], penalty=c["penalty"], sweeps=c["sweeps"],
-                   R=c["R"], seed=c["seed"], L=c["L"], beta=c["beta"])
-    h.run(stream=0)
-    st = h.state(stream=0)
-    E = h.energies(stream=0)
-    for inst, (r0, r1) in [(0, (0, 6)), (1023, (250, 256))]:
-        pb, q = oracle_sqa("me", c["N"], c["J"][inst], c["penalty"], c["L"], c["R"], c["beta"],
-                           c["sweeps"], c["seed"], inst, rho=(r0, r1))
-        got = pkg.unpack_words(st[inst], c["R"])
-        assert np.array_equal(got[:, :, r0:r1], q.s[:, :, r0:r1])
-        for z in (0, 31, 63):
-            assert np.array_equal(E[inst, z, r0:r1], pb.energies(got[z])[r0:r1])
 
 
 @pytest.mark.parametrize("emb,use_table,wc", [("lhz", 0, 0), ("lhz", 1, 0), ("me", 0, 1), ("me", 1, 2),
