@@ -2,11 +2,12 @@
 // autotuner (for one handle and for a batch).
 //
 // A batch fixes a set of handles (SQA or PT jobs of any sizes) and plans
-// them once for the multi-job persistent kernel: every job's units (one
-// instance's run of words) in one list, longest first.  Its first launch
-// captures, on a private stream, the initial-spin kernel of every job, the
-// reset of the work counter and the persistent sweep launch into a CUDA
-// graph; every launch replays that graph on the caller's stream.  An anneal
+// them once for the multi-job persistent kernels: every job's units (one
+// instance's run of words) in one list, grouped by the job's path (PT, SQA
+// windows, SQA tables, ...) and longest first within a path.  Its first
+// launch captures, on a private stream, the initial-spin kernel of every job,
+// the reset of the work counters and one persistent sweep launch per path
+// into a CUDA graph; every launch replays that graph on the caller's stream.  An anneal
 // always starts from its initial spins, so a replay repeats the same anneal
 // bit for bit.
 //
@@ -35,7 +36,7 @@ struct sqa_batch {
     int policy = 0;  // words per unit for every job (0: the planner's choice per job)
     std::vector<JobDev> jobs;
     std::vector<Unit> units;
-    int smem = 0, grid = 1;
+    std::vector<MultiGroup> groups;  // one persistent launch per path
     JobDev *d_jobs = nullptr;
     Unit *d_units = nullptr;
     int *d_counter = nullptr;
@@ -58,7 +59,6 @@ sqa_status plan_batch(sqa_batch *b, int trial)
 {
     b->jobs.clear();
     b->units.clear();
-    b->smem = 0;
     for (size_t k = 0; k < b->hs.size(); k++) {
         sqa_handle *h = b->hs[k];
         JobDev J;
@@ -74,16 +74,12 @@ sqa_status plan_batch(sqa_batch *b, int trial)
         J.t0 = 0;
         J.t1 = trial > 0 ? std::min(trial, h->S) : h->S;
         b->jobs.push_back(J);
-        b->smem = std::max(b->smem, J.smem_bytes);
         for (Unit u : ju) {
             u.job = (int)k;
             b->units.push_back(u);
         }
     }
-    std::stable_sort(b->units.begin(), b->units.end(), [&](const Unit &x, const Unit &y) {
-        const JobDev &p = b->jobs[x.job], &q = b->jobs[y.job];
-        return (double)p.n * p.Z * x.wc * (p.t1 - p.t0) > (double)q.n * q.Z * y.wc * (q.t1 - q.t0);
-    });
+    const int rows = group_units(b->jobs, b->units, b->groups);
     if (b->jobs.size() > b->cap_jobs) {
         if (b->d_jobs) cudaFree(b->d_jobs);
         b->d_jobs = nullptr;
@@ -96,11 +92,11 @@ sqa_status plan_batch(sqa_batch *b, int trial)
         SQA_TRY(cudaMalloc((void **)&b->d_units, b->units.size() * sizeof(Unit)));
         b->cap_units = b->units.size();
     }
-    b->grid = grid_for((const void *)sweep_kernel, b->smem, (int)b->units.size());
-    // one tie queue for the persistent blocks: the largest phase of any job
+    // one tie queue for the persistent blocks of every path's launch: a row
+    // of the largest phase of any job per block
     int stride = 1;
     for (const JobDev &J : b->jobs) stride = std::max(stride, tie_items(J, J.wc));
-    const size_t need = (size_t)b->grid * (size_t)stride;
+    const size_t need = (size_t)rows * (size_t)stride;
     if (need > b->cap_tieq) {
         if (b->d_tieq) cudaFree(b->d_tieq);
         b->d_tieq = nullptr;
@@ -108,25 +104,20 @@ sqa_status plan_batch(sqa_batch *b, int trial)
         SQA_TRY(cudaMalloc((void **)&b->d_tieq, need * sizeof(uint2)));
         b->cap_tieq = need;
     }
-    for (JobDev &J : b->jobs) {
-        J.tieq = b->d_tieq;
-        J.tieq_stride = stride;
-    }
+    assign_tieq(b->jobs, b->groups, b->d_tieq, stride);
     SQA_TRY(cudaMemcpy(b->d_jobs, b->jobs.data(), b->jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice));
     SQA_TRY(cudaMemcpy(b->d_units, b->units.data(), b->units.size() * sizeof(Unit), cudaMemcpyHostToDevice));
     drop_graph(b);
     return SQA_OK;
 }
 
-// Initial spins of every job, then the persistent sweep launch, on s.
+// Initial spins of every job, then one persistent sweep launch per path, on s.
 sqa_status launch_plain(sqa_batch *b, cudaStream_t s)
 {
     sqa_status st;
     for (sqa_handle *h : b->hs)
         if ((st = launch_init(h, s)) != SQA_OK) return st;
-    SQA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(int), s));
-    sweep_kernel<<<b->grid, kThreads, b->smem, s>>>(b->d_jobs, b->d_units, (int)b->units.size(), b->d_counter);
-    SQA_TRY(cudaGetLastError());
+    SQA_TRY(launch_groups(b->groups, b->d_jobs, b->d_units, b->d_counter, s));
     return SQA_OK;
 }
 
@@ -206,7 +197,7 @@ sqa_status sqa_batch_create(sqa_handle *const *hs, int32_t n, sqa_batch **out)
     sqa_batch *b = new (std::nothrow) sqa_batch();
     if (!b) return SQA_ERR_NOMEM;
     b->hs.assign(hs, hs + n);
-    cudaError_t e = cudaMalloc((void **)&b->d_counter, sizeof(int));
+    cudaError_t e = cudaMalloc((void **)&b->d_counter, kMaxModes * sizeof(int));
     sqa_status st = e == cudaSuccess ? plan_batch(b, 0) : cuda_fail(e, "sqa_batch_create");
     if (st != SQA_OK) {
         sqa_batch_destroy(b);

@@ -18,10 +18,9 @@
 namespace sqa {
 
 __global__ void init_kernel(JobDev J, const int *canon);
-__global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units, int *counter);
 // The single-job sweep kernel (kernels.cu), one instantiation per path.
 const void *sweep_one_entry(const JobDev &J);
-const void *sweep_one_entry_mode(int mode);
+
 // Threads per block of the single-job kernel on a job's path.
 int sweep_one_threads(const JobDev &J);
 cudaError_t launch_sweep_one(const JobDev &J, const Unit *units, int n_units, int *counter, int grid,
@@ -64,12 +63,12 @@ sqa_status device_ready()
     if (g_num_sms == 0) {
         cudaDeviceProp prop;
         SQA_CUDA(cudaGetDeviceProperties(&prop, dev));
-        cudaFuncAttributes fa;
-        SQA_CUDA(cudaFuncGetAttributes(&fa, sweep_kernel));
-        const void *ks[8] = {(const void *)sweep_kernel,   sweep_one_entry_mode(0), sweep_one_entry_mode(1),
-                             sweep_one_entry_mode(2), sweep_one_entry_mode(3), sweep_one_entry_mode(4),
-                             sweep_one_entry_mode(5), sweep_one_entry_mode(6)};
-        int limit = (int)prop.sharedMemPerBlockOptin - (int)fa.sharedSizeBytes;
+        const void *ks[14];
+        for (int m = 0; m < kMaxModes; m++) {
+            ks[m] = sweep_one_entry_mode(m);
+            ks[kMaxModes + m] = sweep_multi_entry(m);
+        }
+        int limit = (int)prop.sharedMemPerBlockOptin;
         for (const void *k : ks) {
             cudaFuncAttributes fk;
             SQA_CUDA(cudaFuncGetAttributes(&fk, k));
@@ -78,7 +77,7 @@ sqa_status device_ready()
         for (const void *k : ks) SQA_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
         // single-job kernels may run 16-block clusters (one unit over 16 SMs'
         // worth of blocks); where the device refuses, clusters stop at 8
-        for (int m = 0; m < 7; m++)
+        for (int m = 0; m < kMaxModes; m++)
             if (cudaFuncSetAttribute(sweep_one_entry_mode(m), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                 cudaSuccess)
                 cudaGetLastError();
@@ -558,6 +557,120 @@ int grid_for(const void *kernel, int smem_bytes, int n_units, int threads)
     return std::max(1, std::min(n_units, per_sm * g_num_sms));
 }
 
+int group_units(const std::vector<JobDev> &jobs, std::vector<Unit> &units, std::vector<MultiGroup> &groups)
+{
+    // by path, then longest units first so the tail of each launch is short
+    std::stable_sort(units.begin(), units.end(), [&](const Unit &a, const Unit &b) {
+        const JobDev &x = jobs[a.job], &y = jobs[b.job];
+        const int ma = sweep_mode(x), mb = sweep_mode(y);
+        if (ma != mb) return ma < mb;
+        const double ca = (double)x.n * x.Z * a.wc * (x.t1 - x.t0);
+        const double cb = (double)y.n * y.Z * b.wc * (y.t1 - y.t0);
+        return ca > cb;
+    });
+    groups.clear();
+    for (size_t i = 0; i < units.size();) {
+        const int mode = sweep_mode(jobs[units[i].job]);
+        size_t j = i;
+        int smem = 0;
+        while (j < units.size() && sweep_mode(jobs[units[j].job]) == mode) smem = std::max(smem, jobs[units[j++].job].smem_bytes);
+        MultiGroup g;
+        g.mode = mode;
+        g.u0 = (int)i;
+        g.n = (int)(j - i);
+        g.smem = smem;
+        g.grid = grid_for(sweep_multi_entry(mode), smem, g.n, sweep_mode_threads(mode));
+        g.row0 = 0;
+        groups.push_back(g);
+        i = j;
+    }
+    // the path with the most work starts first; the others fill its tail
+    std::vector<double> work(groups.size(), 0.0);
+    for (size_t k = 0; k < groups.size(); k++)
+        for (int u = groups[k].u0; u < groups[k].u0 + groups[k].n; u++) {
+            const JobDev &x = jobs[units[u].job];
+            work[k] += (double)x.n * x.Z * units[u].wc * (x.t1 - x.t0);
+        }
+    std::vector<size_t> order(groups.size());
+    for (size_t k = 0; k < order.size(); k++) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+    std::vector<MultiGroup> sorted;
+    int rows = 0;  // concurrent launches: each path's blocks get their own tie-queue rows
+    for (size_t k : order) {
+        sorted.push_back(groups[k]);
+        sorted.back().row0 = rows;
+        rows += groups[k].grid;
+    }
+    groups.swap(sorted);
+    return rows;
+}
+
+namespace {
+// Streams and events of this host thread for forking a batch's path launches
+// off the caller's stream (one set per device).
+struct ForkPool {
+    cudaStream_t st[kMaxModes] = {};
+    cudaEvent_t fork = nullptr, join[kMaxModes] = {};
+};
+
+cudaError_t fork_pool(ForkPool **out)
+{
+    thread_local std::vector<ForkPool> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((int)pools.size() <= dev) pools.resize(dev + 1);
+    ForkPool &p = pools[dev];
+    if (!p.fork) {
+        for (int k = 0; k < kMaxModes && e == cudaSuccess; k++) {
+            e = cudaStreamCreateWithFlags(&p.st[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.join[k], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    *out = &p;
+    return cudaSuccess;
+}
+}  // namespace
+
+void assign_tieq(std::vector<JobDev> &jobs, const std::vector<MultiGroup> &groups, uint2 *d_tieq, int stride)
+{
+    for (JobDev &J : jobs) {
+        J.tieq = d_tieq;
+        J.tieq_stride = stride;
+        for (const MultiGroup &g : groups)
+            if (g.mode == sweep_mode(J)) J.tieq = d_tieq + (size_t)g.row0 * (size_t)stride;
+    }
+}
+
+cudaError_t launch_groups(const std::vector<MultiGroup> &groups, const JobDev *d_jobs, const Unit *d_units,
+                          int *d_counters, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(d_counters, 0, kMaxModes * sizeof(int), s);
+    if (e != cudaSuccess || groups.empty()) return e;
+    if (groups.size() == 1) {
+        const MultiGroup &g = groups[0];
+        return launch_sweep_multi(g.mode, g.grid, g.smem, d_jobs, d_units + g.u0, g.n, d_counters + g.mode, s);
+    }
+    // several paths: each persistent launch on its own stream after the
+    // caller's stream, all joined back into it, so that blocks of the next
+    // path take the SMs the previous path's blocks leave at the end of its
+    // work (the paths' tails overlap instead of running one after another)
+    ForkPool *p = nullptr;
+    if ((e = fork_pool(&p)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(p->fork, s)) != cudaSuccess) return e;
+    for (size_t k = 0; k < groups.size() && e == cudaSuccess; k++) {
+        const MultiGroup &g = groups[k];
+        e = cudaStreamWaitEvent(p->st[k], p->fork, 0);
+        if (e == cudaSuccess)
+            e = launch_sweep_multi(g.mode, g.grid, g.smem, d_jobs, d_units + g.u0, g.n, d_counters + g.mode, p->st[k]);
+        if (e == cudaSuccess) e = cudaEventRecord(p->join[k], p->st[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join[k], 0);
+    }
+    return e;
+}
+
 int launch_grid(const JobDev &J, int n_units)
 {
     if (J.csize == 1) return grid_for(sweep_one_entry(J), J.smem_bytes, n_units, sweep_one_threads(J));
@@ -874,7 +987,6 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<JobDev> jobs;
     std::vector<Unit> units;
-    int smem = 0;
     sqa_status st;
     for (int k = 0; k < n; k++) {
         sqa_handle *h = hs[k];
@@ -888,43 +1000,29 @@ sqa_status sqa_batch_run(sqa_handle *const *hs, int32_t n, void *stream)
         J.t0 = 0;
         J.t1 = h->S;
         jobs.push_back(J);
-        smem = std::max(smem, J.smem_bytes);
         for (Unit u : ju) {
             u.job = k;
             units.push_back(u);
         }
     }
-    // longest units first so the tail of the launch is short
-    std::stable_sort(units.begin(), units.end(), [&](const Unit &a, const Unit &b) {
-        const JobDev &x = jobs[a.job], &y = jobs[b.job];
-        const double ca = (double)x.n * x.Z * a.wc * (x.t1 - x.t0);
-        const double cb = (double)y.n * y.Z * b.wc * (y.t1 - y.t0);
-        return ca > cb;
-    });
+    std::vector<MultiGroup> groups;
+    const int rows = group_units(jobs, units, groups);
     JobDev *d_jobs = nullptr;
     Unit *d_units = nullptr;
     int *d_counter = nullptr;
     uint2 *d_tieq = nullptr;
-    const int grid = grid_for((const void *)sweep_kernel, smem, (int)units.size());
     int stride = 1;
     for (const JobDev &J : jobs) stride = std::max(stride, tie_items(J, J.wc));
-    cudaError_t e = cudaMallocAsync((void **)&d_tieq, (size_t)grid * stride * sizeof(uint2), s);
-    for (JobDev &J : jobs) {
-        J.tieq = d_tieq;
-        J.tieq_stride = stride;
-    }
+    cudaError_t e = cudaMallocAsync((void **)&d_tieq, (size_t)rows * stride * sizeof(uint2), s);
+    assign_tieq(jobs, groups, d_tieq, stride);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_jobs, jobs.size() * sizeof(JobDev), s);
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_units, units.size() * sizeof(Unit), s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_counter, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_counter, kMaxModes * sizeof(int), s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(JobDev), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(int), s);
-    if (e == cudaSuccess) {
-        sweep_kernel<<<grid, kThreads, smem, s>>>(d_jobs, d_units, (int)units.size(), d_counter);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = launch_groups(groups, d_jobs, d_units, d_counter, s);
     // freed in stream order after the launch (or at once on an error); host
     // vectors are consumed: pageable copies are staged before return
     if (d_tieq) cudaFreeAsync(d_tieq, s);

@@ -75,8 +75,34 @@ sqa_status cuda_fail(cudaError_t e, const char *where);
 sqa_status launch_init(sqa_handle *h, cudaStream_t s);
 // Blocks for one launch of kernel over n_units units (at most one wave).
 int grid_for(const void *kernel, int smem_bytes, int n_units, int threads = kThreads);
-// The multi-job sweep kernel (kernels.cu).
-__global__ void sweep_kernel(const JobDev *jobs, const Unit *units, int n_units, int *counter);
+// The sweep kernels' paths (kernels.cu): 0 PT, 1 SQA windows, 2 SQA tables,
+// 3 / 4 SQA cluster moves (L <= 64 / L <= 128), 5 SQA tables of two-spin
+// terms, 6 PT of two-spin terms; each path has a single-job and a multi-job
+// kernel, and its own block size.
+constexpr int kMaxModes = 7;
+int sweep_mode(const JobDev &J);
+int sweep_mode_threads(int mode);
+const void *sweep_one_entry_mode(int mode);
+const void *sweep_multi_entry(int mode);
+// One persistent launch of the multi-job kernel of a path over n_units units
+// (each names its job in jobs), pulling units from *counter.
+cudaError_t launch_sweep_multi(int mode, int grid, int smem, const JobDev *jobs, const Unit *units, int n_units,
+                               int *counter, cudaStream_t s);
+// The units of a mixed batch, one run per path: units[u0, u0 + n) run in one
+// launch of that path's multi-job kernel with grid blocks of smem bytes.
+// The launches run concurrently, so each has its own rows of the tie queue
+// (JobDev::tieq), from row row0.
+struct MultiGroup {
+    int mode, u0, n, smem, grid, row0;
+};
+// Sorts units by path (longest first within a path) into groups, sizes their
+// launches and orders them by work; returns the tie-queue rows of all groups.
+int group_units(const std::vector<JobDev> &jobs, std::vector<Unit> &units, std::vector<MultiGroup> &groups);
+// Points every job's tie queue at its group's rows of d_tieq (stride entries a row).
+void assign_tieq(std::vector<JobDev> &jobs, const std::vector<MultiGroup> &groups, uint2 *d_tieq, int stride);
+// Zeroes the kMaxModes counters and launches every group in order on s.
+cudaError_t launch_groups(const std::vector<MultiGroup> &groups, const JobDev *d_jobs, const Unit *d_units,
+                          int *d_counters, cudaStream_t s);
 // Device bytes sqa_create would allocate for desc (host-only estimate, exact
 // for the state and tables).
 int64_t estimate_device_bytes(const sqa_desc *d);

@@ -1408,10 +1408,14 @@ int max_active_clusters(const JobDev &J)
     return n;
 }
 
-// Several jobs of any shapes (each unit in one block): each unit names its
-// job; the block copies that job's descriptor into shared memory.
-__global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const Unit *units, int n_units,
-                                                       int *counter)
+// Several jobs of one path (each unit in one block): each unit names its
+// job; the block copies that job's descriptor into shared memory.  One
+// instantiation per path, with the registers and blocks per SM of the
+// single-job kernel of that path; a batch of mixed paths runs one
+// persistent launch per path, one after another.
+template <int MODE>
+__global__ void __launch_bounds__(MODE == 0 || MODE == 6 ? 384 : 256, MODE == 3 ? 4 : (MODE == 0 || MODE == 6 ? 2 : 3))
+    sweep_kernel_multi(const JobDev *jobs, const Unit *units, int n_units, int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_unit;
@@ -1426,22 +1430,55 @@ __global__ void __launch_bounds__(256, 2) sweep_kernel(const JobDev *jobs, const
         if (s_job.csize != 1) continue;  // units of this kernel live in one block
         const Unit u = units[ui];
         const Smem sm = carve(s_job, smem_raw);
-        if (s_job.kind == SQA_KIND_PT && s_job.pairs)
-            run_unit<SQA_KIND_PT, false, true>(s_job, sm, u);
-        else if (s_job.kind == SQA_KIND_PT)
+        if (MODE == 0)
             run_unit<SQA_KIND_PT, false, false>(s_job, sm, u);
-        else if (s_job.move == SQA_MOVE_WOLFF && s_job.Z <= 64)
-            run_unit_wolff<2>(s_job, sm, u);
-        else if (s_job.move == SQA_MOVE_WOLFF)
-            run_unit_wolff<4>(s_job, sm, u);
-        else if (s_job.use_lut && s_job.pairs)
-            run_unit<SQA_KIND_SQA, true, true>(s_job, sm, u);
-        else if (s_job.use_lut)
+        else if (MODE == 6)
+            run_unit<SQA_KIND_PT, false, true>(s_job, sm, u);
+        else if (MODE == 2)
             run_unit<SQA_KIND_SQA, true, false>(s_job, sm, u);
+        else if (MODE == 5)
+            run_unit<SQA_KIND_SQA, true, true>(s_job, sm, u);
+        else if (MODE == 3)
+            run_unit_wolff<2>(s_job, sm, u);
+        else if (MODE == 4)
+            run_unit_wolff<4>(s_job, sm, u);
         else
             run_unit<SQA_KIND_SQA, false, false>(s_job, sm, u);
         __syncthreads();
     }
+}
+
+int sweep_mode(const JobDev &J) { return one_mode(J); }
+
+int sweep_mode_threads(int mode) { return mode == 0 || mode == 6 ? 384 : 256; }
+
+const void *sweep_multi_entry(int mode)
+{
+    switch (mode) {
+    case 0: return (const void *)sweep_kernel_multi<0>;
+    case 1: return (const void *)sweep_kernel_multi<1>;
+    case 2: return (const void *)sweep_kernel_multi<2>;
+    case 3: return (const void *)sweep_kernel_multi<3>;
+    case 4: return (const void *)sweep_kernel_multi<4>;
+    case 5: return (const void *)sweep_kernel_multi<5>;
+    default: return (const void *)sweep_kernel_multi<6>;
+    }
+}
+
+cudaError_t launch_sweep_multi(int mode, int grid, int smem, const JobDev *jobs, const Unit *units, int n_units,
+                               int *counter, cudaStream_t s)
+{
+    const dim3 g((unsigned)grid), b((unsigned)sweep_mode_threads(mode));
+    switch (mode) {
+    case 0: sweep_kernel_multi<0><<<g, b, smem, s>>>(jobs, units, n_units, counter); break;
+    case 1: sweep_kernel_multi<1><<<g, b, smem, s>>>(jobs, units, n_units, counter); break;
+    case 2: sweep_kernel_multi<2><<<g, b, smem, s>>>(jobs, units, n_units, counter); break;
+    case 3: sweep_kernel_multi<3><<<g, b, smem, s>>>(jobs, units, n_units, counter); break;
+    case 4: sweep_kernel_multi<4><<<g, b, smem, s>>>(jobs, units, n_units, counter); break;
+    case 5: sweep_kernel_multi<5><<<g, b, smem, s>>>(jobs, units, n_units, counter); break;
+    default: sweep_kernel_multi<6><<<g, b, smem, s>>>(jobs, units, n_units, counter); break;
+    }
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
