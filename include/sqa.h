@@ -296,16 +296,31 @@ typedef struct {
      * waiting for the GPU */
     double admit_s, advance_s, idle_s;
     int32_t worker_status, pad_;
+    /* packed launches of small jobs' chunks (multi-job kernels), and the
+     * worker time spent building and launching them and retiring jobs (parts
+     * of advance_s) */
+    int64_t packs;
+    double pack_s, retire_s;
+    double create_s;  /* part of admit_s: creating handles (planning, tables, uploads) */
+    double pad2_;
 } sqa_server_stats;
 
 /* A server owns a worker thread that serves jobs on the current device.  It
  * admits queued jobs in arrival order while their device memory fits
- * mem_budget_bytes (a job larger than the budget fails with SQA_ERR_NOMEM),
- * runs each resident job as a chain of launches ("chunks") of its own sweep
- * kernel on a stream of its own, about unit_attempts_per_chunk attempts per
- * work unit each (0 picks a default), so that all resident jobs share the GPU
- * and none waits for another, and retires finished jobs (state and energies
- * copied to host, device memory freed in stream order).  Results are
+ * mem_budget_bytes (a job larger than the budget fails with SQA_ERR_NOMEM)
+ * and runs each resident job as a chain of chunks of its sweeps, about
+ * unit_attempts_per_chunk attempts per work unit each (0 picks 1e7).  Jobs
+ * whose work units fit one block each are packed: whenever jobs are ready for
+ * their next chunk, the chunks of all of them on one path (PT, SQA tables,
+ * SQA windows, ...) go into one launch of that path's multi-job kernel, and
+ * several packs run at once on different streams; jobs that need thread-block
+ * clusters run their chunks as launches of their own sweep kernel on
+ * higher-priority streams.  Admission never waits on the GPU: a job's tables
+ * are uploaded from pinned memory on a stream of their own and its initial
+ * spins are drawn just before its first chunk.  A finished job's energies and
+ * state are copied to pinned host memory behind its final chunk, and the job
+ * is retired (results kept on the host, device memory freed in stream order)
+ * once those copies have landed.  Results are
  * bit-identical to sqa_run of the same descriptor, whatever else was
  * resident.  The server keeps up to mem_budget_bytes of freed memory in the
  * device's default stream-ordered memory pool for reuse. */

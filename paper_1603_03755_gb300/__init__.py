@@ -320,7 +320,8 @@ class _ServerStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("jobs_submitted", "jobs_done", "jobs_failed", "chunks", "attempts",
                                          "resident", "queued", "max_resident", "bytes_in_use", "max_bytes")] + \
                [(n, C.c_double) for n in ("admit_s", "advance_s", "idle_s")] + \
-               [("worker_status", C.c_int32), ("pad_", C.c_int32)]
+               [("worker_status", C.c_int32), ("pad_", C.c_int32), ("packs", C.c_int64),
+                ("pack_s", C.c_double), ("retire_s", C.c_double), ("create_s", C.c_double), ("pad2_", C.c_double)]
 
 
 JOB_STATES = ("queued", "running", "done", "failed")
@@ -371,7 +372,7 @@ class Server:
     def stats(self) -> dict:
         st = _ServerStats()
         _check(lib().sqa_server_get_stats(self._s, C.byref(st)), "sqa_server_get_stats")
-        return {k: getattr(st, k) for k, _ in _ServerStats._fields_ if k != "pad_"}
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_ if not k.startswith("pad")}
 
     def close(self):
         if getattr(self, "_s", None):

@@ -49,6 +49,8 @@ sqa_status cuda_fail(cudaError_t e, const char *where)
     } while (0)
 
 static int g_num_sms = 0;
+
+int num_sms() { return g_num_sms; }
 static int g_smem_limit = 0;  // dynamic shared memory one sweep block may use
 
 sqa_status device_ready()
@@ -107,7 +109,7 @@ sqa_status dalloc(sqa_handle *h, T **p, size_t count)
     void *q = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
     // stream-ordered: freeing later needs no device-wide synchronization
-    cudaError_t e = cudaMallocAsync(&q, bytes, 0);
+    cudaError_t e = cudaMallocAsync(&q, bytes, h->setup_stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         g_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -126,6 +128,51 @@ sqa_status upload(sqa_handle *h, T **p, const std::vector<T> &v)
     if (st != SQA_OK) return st;
     if (!v.empty()) SQA_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
     h->h2d_bytes += (int64_t)(v.size() * sizeof(T));
+    return SQA_OK;
+}
+
+// Host arrays gathered for one upload: every array at a 256-byte aligned
+// offset of one staging buffer, copied by one cudaMemcpy into one device
+// allocation (a synchronous copy can wait behind work other streams queued
+// on the same hardware queue, so a handle's setup makes as few as it can).
+struct Staging {
+    std::vector<unsigned char> host;
+    std::vector<std::pair<void **, size_t>> fix;  // where each array's device address goes, its offset
+    int64_t counted = 0, bytes = 0;               // device bytes as separate allocations would count, payload
+};
+
+template <typename T>
+void stage(Staging &sg, T **p, const std::vector<T> &v)
+{
+    const size_t off = (sg.host.size() + 255) & ~(size_t)255;
+    const size_t b = v.size() * sizeof(T);
+    sg.host.resize(off + std::max<size_t>(b, sizeof(T)));
+    if (b) memcpy(sg.host.data() + off, v.data(), b);
+    sg.fix.emplace_back((void **)p, off);
+    sg.counted += (int64_t)(std::max<size_t>(v.size(), 1) * sizeof(T));
+    sg.bytes += (int64_t)b;
+}
+
+sqa_status commit(sqa_handle *h, Staging &sg)
+{
+    unsigned char *q = nullptr;
+    const cudaError_t e = cudaMallocAsync((void **)&q, std::max<size_t>(sg.host.size(), 1), h->setup_stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        g_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return SQA_ERR_NOMEM;
+    }
+    h->allocs.push_back(q);
+    h->device_bytes += sg.counted;
+    for (auto &f : sg.fix) *f.first = q + f.second;
+    h->h2d_bytes += sg.bytes;
+    if (h->lazy_tieq) {
+        // served job: the caller queues the copy (pending_upload)
+        h->pending.swap(sg.host);
+        h->pending_dst = q;
+        return SQA_OK;
+    }
+    if (!sg.host.empty()) SQA_CUDA(cudaMemcpy(q, sg.host.data(), sg.host.size(), cudaMemcpyHostToDevice));
     return SQA_OK;
 }
 
@@ -449,31 +496,35 @@ sqa_status setup_program(sqa_handle *h)
     }
     sqa_status st;
     if ((st = dalloc(h, &h->d_state, (size_t)h->I * J.Z * J.n * J.W)) != SQA_OK) return st;
-    if ((st = upload(h, &h->d_sites, all_sites)) != SQA_OK) return st;
-    if ((st = upload(h, &h->d_eterms, all_et)) != SQA_OK) return st;
-    if ((st = upload(h, &h->d_ecls, all_ec)) != SQA_OK) return st;
+    Staging sg;
+    stage(sg, &h->d_sites, all_sites);
+    stage(sg, &h->d_eterms, all_et);
+    stage(sg, &h->d_ecls, all_ec);
     J.n_ecls = ecls_ok ? n_ecls : 0;
     if (wolff) {
-        if ((st = upload(h, &h->d_Tb, Tb)) != SQA_OK) return st;
-        if ((st = upload(h, &h->d_Tacc, Tacc)) != SQA_OK) return st;
-        if ((st = upload(h, &h->d_accoff, accoff)) != SQA_OK) return st;
-        if ((st = upload(h, &h->d_acclen, acclen)) != SQA_OK) return st;
-    } else if ((st = upload(h, &h->d_T, T)) != SQA_OK) {
-        return st;
+        stage(sg, &h->d_Tb, Tb);
+        stage(sg, &h->d_Tacc, Tacc);
+        stage(sg, &h->d_accoff, accoff);
+        stage(sg, &h->d_acclen, acclen);
+    } else {
+        stage(sg, &h->d_T, T);
     }
     if (h->kind == SQA_KIND_PT) {
-        if ((st = upload(h, &h->d_Tsw, Tsw)) != SQA_OK) return st;
-        if ((st = upload(h, &h->d_swoff, swoff)) != SQA_OK) return st;
-        if ((st = upload(h, &h->d_swlen, swlen)) != SQA_OK) return st;
+        stage(sg, &h->d_Tsw, Tsw);
+        stage(sg, &h->d_swoff, swoff);
+        stage(sg, &h->d_swlen, swlen);
     }
-    if ((st = upload(h, &h->d_canon, pl.canon)) != SQA_OK) return st;
-    if ((st = upload(h, &h->d_compact, pl.compact)) != SQA_OK) return st;
-    if ((st = upload(h, &h->d_J, h->J)) != SQA_OK) return st;
-    if (h->emb == SQA_EMB_ME_CHIMERA) {
-        if ((st = upload(h, &h->d_chain, pl.chain)) != SQA_OK) return st;
-    } else {
-        if ((st = upload(h, &h->d_pair, pl.pair)) != SQA_OK) return st;
-    }
+    stage(sg, &h->d_canon, pl.canon);
+    stage(sg, &h->d_compact, pl.compact);
+    stage(sg, &h->d_J, h->J);
+    if (h->emb == SQA_EMB_ME_CHIMERA)
+        stage(sg, &h->d_chain, pl.chain);
+    else
+        stage(sg, &h->d_pair, pl.pair);
+    if ((st = plan_units(h)) != SQA_OK) return st;
+    stage(sg, &h->d_units, h->units);
+    h->units_staged = true;
+    if ((st = commit(h, sg)) != SQA_OK) return st;
     h->cur_trees = -1;
     J.state = h->d_state;
     J.sites = h->d_sites;
@@ -487,15 +538,8 @@ sqa_status setup_program(sqa_handle *h)
     J.Tacc = h->d_Tacc;
     J.acc_off = h->d_accoff;
     J.acc_len = h->d_acclen;
-    if ((st = plan_units(h)) != SQA_OK) return st;
-    {
-        const int64_t ne = tieq_entries(h->plan, h->kind, h->move, h->I, h->job.Z, h->job.W);
-        if (ne > 0 && (st = dalloc(h, &h->d_tieq, (size_t)ne)) != SQA_OK) return st;
-        h->tieq_cap = (size_t)ne;
-        set_tieq(h);
-    }
+    if (!h->lazy_tieq && (st = ensure_tieq(h)) != SQA_OK) return st;
     if ((st = dalloc(h, &h->d_job, 1)) != SQA_OK) return st;
-    if ((st = upload(h, &h->d_units, h->units)) != SQA_OK) return st;
     h->n_units = (int)h->units.size();
     if ((st = dalloc(h, &h->d_counter, 1)) != SQA_OK) return st;
     h->ready = true;
@@ -504,6 +548,8 @@ sqa_status setup_program(sqa_handle *h)
 
 sqa_status launch_sweeps(sqa_handle *h, int t0, int t1, int u0, int nu, cudaStream_t s)
 {
+    const sqa_status sq = ensure_tieq(h);  // a served handle allocates it on its first own launch
+    if (sq != SQA_OK) return sq;
     if (!h->d_units || u0 < 0 || nu < 0 || u0 + nu > h->n_units)
         return set_error("no unit list on the device (a failed sqa_tune)"), SQA_ERR_INVALID;
     h->job.t0 = t0;
@@ -645,13 +691,16 @@ void assign_tieq(std::vector<JobDev> &jobs, const std::vector<MultiGroup> &group
 }
 
 cudaError_t launch_groups(const std::vector<MultiGroup> &groups, const JobDev *d_jobs, const Unit *d_units,
-                          int *d_counters, cudaStream_t s)
+                          int *d_counters, cudaStream_t s, bool fork)
 {
     cudaError_t e = cudaMemsetAsync(d_counters, 0, kMaxModes * sizeof(int), s);
     if (e != cudaSuccess || groups.empty()) return e;
-    if (groups.size() == 1) {
-        const MultiGroup &g = groups[0];
-        return launch_sweep_multi(g.mode, g.grid, g.smem, d_jobs, d_units + g.u0, g.n, d_counters + g.mode, s);
+    if (groups.size() == 1 || !fork) {
+        for (size_t k = 0; k < groups.size() && e == cudaSuccess; k++) {
+            const MultiGroup &g = groups[k];
+            e = launch_sweep_multi(g.mode, g.grid, g.smem, d_jobs, d_units + g.u0, g.n, d_counters + g.mode, s);
+        }
+        return e;
     }
     // several paths: each persistent launch on its own stream after the
     // caller's stream, all joined back into it, so that blocks of the next
@@ -765,9 +814,22 @@ const char *sqa_strerror(sqa_status s)
 
 const char *sqa_last_error(void) { return g_err.c_str(); }
 
-sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
+}  // extern "C"
+
+namespace sqa {
+sqa_status ensure_tieq(sqa_handle *h)
 {
-    NvtxScope nvtx_("sqa_create");
+    if (h->d_tieq || h->tieq_cap) return SQA_OK;
+    const int64_t ne = tieq_entries(h->plan, h->kind, h->move, h->I, h->job.Z, h->job.W);
+    sqa_status st;
+    if (ne > 0 && (st = dalloc(h, &h->d_tieq, (size_t)ne)) != SQA_OK) return st;
+    h->tieq_cap = (size_t)ne;
+    set_tieq(h);
+    return SQA_OK;
+}
+
+sqa_status create_handle(const sqa_desc *d, sqa_handle **out, bool init, cudaStream_t setup_stream)
+{
     if (!out) return set_error("out is NULL"), SQA_ERR_INVALID;
     *out = nullptr;
     sqa_status st = validate(d);
@@ -776,6 +838,8 @@ sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
     sqa_handle *h = new (std::nothrow) sqa_handle();
     if (!h) return SQA_ERR_NOMEM;
     h->kind = d->kind;
+    h->lazy_tieq = !init;
+    h->setup_stream = init ? (cudaStream_t)0 : setup_stream;
     h->emb = d->embedding;
     h->N = d->n_logical;
     h->I = d->n_instances;
@@ -812,11 +876,16 @@ sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
         return set_error(err), SQA_ERR_UNSUPPORTED;
     }
     st = setup_program(h);
-    if (st == SQA_OK) st = launch_init(h, 0);
-    if (st == SQA_OK) {
+    if (st == SQA_OK && init) st = launch_init(h, 0);
+    if (st == SQA_OK && init) {
         // the legacy stream: waits for this handle's work only, not for work
         // on non-blocking streams (the serving loop's chunks in flight)
         cudaError_t e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) st = cuda_fail(e, "sqa_create");
+    } else if (st == SQA_OK) {
+        // no wait on the host: the caller queues the upload on setup_stream
+        // (pending_upload) and its first user's stream waits for setup_ev
+        const cudaError_t e = cudaEventCreateWithFlags(&h->setup_ev, cudaEventDisableTiming);
         if (e != cudaSuccess) st = cuda_fail(e, "sqa_create");
     }
     if (st != SQA_OK) {
@@ -828,10 +897,21 @@ sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
     return SQA_OK;
 }
 
+}  // namespace sqa
+
+extern "C" {
+
+sqa_status sqa_create(const sqa_desc *d, sqa_handle **out)
+{
+    NvtxScope nvtx_("sqa_create");
+    return create_handle(d, out, true, 0);
+}
+
 void sqa_destroy(sqa_handle *h)
 {
     if (!h) return;
     cudaDeviceSynchronize();
+    if (h->setup_ev) cudaEventDestroy(h->setup_ev);
     free_all(h);
     cudaStreamSynchronize(0);
     delete h;
@@ -845,9 +925,19 @@ namespace sqa {
 void destroy_on_stream(sqa_handle *h, cudaStream_t s)
 {
     if (!h) return;
+    if (h->setup_ev) cudaEventDestroy(h->setup_ev);
     free_all(h, s);
     delete h;
 }
+
+cudaError_t enqueue_energies(const sqa_handle *h, int32_t *dev_out, cudaStream_t s)
+{
+    const size_t count = (size_t)h->I * h->job.Z * h->R;
+    const int blocks = (int)std::min<size_t>((count + kThreads - 1) / kThreads, 8192);
+    energy_kernel<<<std::max(blocks, 1), kThreads, 0, s>>>(h->job, dev_out);
+    return cudaGetLastError();
+}
+
 }  // namespace sqa
 
 extern "C" {
@@ -869,6 +959,7 @@ sqa_status sqa_get_info(const sqa_handle *h, sqa_info *o)
     o->pad_ = 0;
     return SQA_OK;
 }
+
 
 sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, int32_t cluster)
 {
@@ -895,9 +986,12 @@ sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, in
     }
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "sqa_tune");
-    SQA_CUDA(cudaFreeAsync(h->d_units, 0));
-    for (auto &p : h->allocs)
-        if (p == (void *)h->d_units) p = nullptr;
+    if (!h->units_staged) {  // a list inside the setup's one upload stays until the handle goes
+        SQA_CUDA(cudaFreeAsync(h->d_units, 0));
+        for (auto &p : h->allocs)
+            if (p == (void *)h->d_units) p = nullptr;
+    }
+    h->units_staged = false;
     h->device_bytes -= (int64_t)(std::max<size_t>(keep_units.size(), 1) * sizeof(Unit));
     h->d_units = nullptr;
     h->n_units = 0;  // the handle runs nothing until a unit list is on the device again

@@ -58,6 +58,16 @@ struct sqa_handle {
     int64_t h2d_bytes = 0;
     std::vector<void *> allocs;
     bool ready = false;  // a complete device program is resident (set by its setup)
+    bool lazy_tieq = false;  // setup leaves the tie queue to ensure_tieq (served jobs)
+    bool units_staged = false;  // d_units lies inside the setup's one upload (not freed alone)
+    // served jobs: the setup's allocations and its one upload go on
+    // setup_stream without a host wait; the upload's bytes wait in pending
+    // until the server copies them to pinned memory and queues the copy to
+    // pending_dst, then records setup_ev
+    cudaStream_t setup_stream = nullptr;
+    std::vector<unsigned char> pending;
+    void *pending_dst = nullptr;
+    cudaEvent_t setup_ev = nullptr;
 };
 
 
@@ -66,6 +76,8 @@ namespace sqa {
 constexpr int kThreads = 256;  // threads per block of every kernel here
 
 sqa_status device_ready();
+// SMs of the device (after device_ready).
+int num_sms();
 // SQA_OK when h holds a complete device program (else SQA_ERR_INVALID: NULL,
 // or its last setup failed part way, e.g. a rejected pt_run).
 sqa_status usable(const sqa_handle *h);
@@ -100,9 +112,11 @@ struct MultiGroup {
 int group_units(const std::vector<JobDev> &jobs, std::vector<Unit> &units, std::vector<MultiGroup> &groups);
 // Points every job's tie queue at its group's rows of d_tieq (stride entries a row).
 void assign_tieq(std::vector<JobDev> &jobs, const std::vector<MultiGroup> &groups, uint2 *d_tieq, int stride);
-// Zeroes the kMaxModes counters and launches every group in order on s.
+// Zeroes the kMaxModes counters and launches every group on s: with fork,
+// each on its own stream of this host thread's pool, all joined back into s
+// (the groups run concurrently); otherwise one after another on s.
 cudaError_t launch_groups(const std::vector<MultiGroup> &groups, const JobDev *d_jobs, const Unit *d_units,
-                          int *d_counters, cudaStream_t s);
+                          int *d_counters, cudaStream_t s, bool fork = true);
 // Device bytes sqa_create would allocate for desc (host-only estimate, exact
 // for the state and tables).
 int64_t estimate_device_bytes(const sqa_desc *d);
@@ -112,6 +126,19 @@ void destroy_on_stream(sqa_handle *h, cudaStream_t s);
 int launch_grid(const JobDev &J, int n_units);
 // One launch of a job's own sweep kernel over all its units.
 cudaError_t launch_job_sweeps(const JobDev &J, const Unit *units, int n_units, int *counter, cudaStream_t s);
+// sqa_create; with init false nothing waits on the host: the initial spins
+// are not drawn (the caller launches launch_init on its own stream before
+// the first sweep), allocations are queued on setup_stream and the upload is
+// left in h->pending for the caller to queue from pinned memory, so that
+// creation never waits behind work already on a busy GPU.
+// With init false the tie queue of the handle's own sweep kernel is not
+// allocated either (a served job packed into multi-job launches never uses
+// it; ensure_tieq allocates it before the handle's own first launch).
+sqa_status create_handle(const sqa_desc *d, sqa_handle **out, bool init, cudaStream_t setup_stream);
+sqa_status ensure_tieq(sqa_handle *h);
+// Enqueues on s the energy of every (instance, slice or slot, replica) of h
+// into dev_out (device, [I][Z][R] int32), as sqa_energies computes them.
+cudaError_t enqueue_energies(const sqa_handle *h, int32_t *dev_out, cudaStream_t s);
 // Plans h's launch (J, units) for the multi-job kernel of batches, with
 // c_forced blocks per cluster (0: any) and force_wc words per unit (0: the
 // planner's choice), without changing h.

@@ -52,13 +52,16 @@ def test_served_results_equal_alone_runs():
     for jid, kw, est in zip(ids, jobs, budgets):
         info = srv.poll(jid)
         assert info["state"] == "done"
-        # admission estimate: exact but for the work-unit list, which it
-        # sizes for one unit per 32-replica word (an upper bound)
+        # admission estimate: exact for a handle of its own but for the
+        # work-unit list, which it sizes for one unit per 32-replica word (an
+        # upper bound); a served job packed into multi-job launches holds
+        # less (no tie queue of its own)
         slack = kw["J"].shape[0] * ((kw["R"] + 31) // 32) * 16
-        assert info["device_bytes"] <= est <= info["device_bytes"] + slack
+        assert info["device_bytes"] <= est
         assert info["t_submit"] <= info["t_start"] <= info["t_done"]
         st, en = srv.result(jid)
         h = pkg.Handle(**kw)
+        assert h.info["device_bytes"] <= est <= h.info["device_bytes"] + slack
         h.run(stream=0)
         assert np.array_equal(st, h.state(stream=0)), kw
         assert np.array_equal(en, h.energies(stream=0)), kw
@@ -110,5 +113,29 @@ def test_a_failing_job_fails_alone():
         h = pkg.Handle(**kw)
         h.run(stream=0)
         assert np.array_equal(got, h.state(stream=0))
+        h.close()
+    srv.close()
+
+
+def test_cluster_job_beside_packed_jobs():
+    """A job whose 32-replica word does not fit one block (LHZ K_40, L = 128),
+    so that it runs clusters of its own sweep kernel on a high-priority
+    stream, served beside small jobs packed into multi-job launches: every
+    result equals the job alone."""
+    J40 = W.random_instances(40, 1, 410)
+    big = dict(embedding="lhz", N=40, J=J40, penalty=9, sweeps=16_000, R=32, seed=410, kind="sqa", L=128,
+               beta=10 / 3)
+    small = _jobs()[:3]
+    srv = pkg.Server(mem_budget_bytes=1 << 33)
+    ids = [srv.submit(**kw) for kw in [big] + small]
+    for jid in ids:
+        srv.wait(jid, timeout=600)
+    assert all(srv.poll(jid)["state"] == "done" for jid in ids)
+    for jid, kw in zip(ids, [big] + small):
+        got, en = srv.result(jid)
+        h = pkg.Handle(**kw)
+        h.run(stream=0)
+        assert np.array_equal(got, h.state(stream=0)), kw["N"]
+        assert np.array_equal(en, h.energies(stream=0)), kw["N"]
         h.close()
     srv.close()
