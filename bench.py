@@ -99,7 +99,7 @@ def kernel_capture(n_instances):
     rec = json.load(open(p))
     if rec.get("kernels_cu_code_sha256") != kernels_code_sha256(src):
         return None, "kernel changed since the capture", None
-    counters = {k: rec.get(k) for k in ("instr_per_attempt", "issue_active", "pipe_alu", "pipe_fmaheavy",
+    counters = {k: rec.get(k) for k in ("instr_per_attempt", "issue_active", "pipe_alu", "pipe_fma",
                                         "shared_bank_conflicts_per_wavefront")}
     return rec["dram_bytes_per_instance"] * n_instances, rec["note"], counters
 
@@ -673,7 +673,7 @@ def main():
                      "instr_per_attempt": ipa,
                      "issue_active": (counters or {}).get("issue_active"),
                      "pipes": None if not counters else {"alu": counters.get("pipe_alu"),
-                                                         "fmaheavy": counters.get("pipe_fmaheavy")},
+                                                         "fma": counters.get("pipe_fma")},
                      "counters_source": "ncu capture of the sweep kernel (profiles/sweep_kernel_traffic.json)"
                                         if counters else traffic_note,
                      "mixed_pipe_ceiling": {
