@@ -74,7 +74,10 @@ typedef enum {
     SQA_DECODE_LHZ_CHAIN = 3, /* LHZ chain tree q_i = prod_{m<i} q_{m,m+1} (Eq. 10) */
     SQA_DECODE_LHZ_MWD = 4,   /* LHZ minimum-weight decoding (Sec. IV A), exact by enumeration, N <= 24:
                                  the logical state whose pair products disagree with the fewest pair
-                                 spins; q_{N-1} = +1, ties to the first state in binary order */
+                                 spins; q_{N-1} = +1, ties to the first state in binary order.  N > 24
+                                 (2^23 states per replica and more) -> SQA_ERR_UNSUPPORTED: larger LHZ
+                                 problems (the serving stream draws N up to 40) decode with the tree,
+                                 vote or belief-propagation methods */
     SQA_DECODE_LHZ_BP = 5     /* LHZ belief propagation (Sec. IV, App. C), N <= 32, error rate 0.2 and
                                  10 iterations (sqa_decode_bp for others), read out by random tree 0 */
 } sqa_decode_method;
