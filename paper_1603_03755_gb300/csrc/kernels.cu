@@ -15,20 +15,20 @@
 // colour classes (SQA: colour x slice parity; PT: colour) run in order with a
 // barrier between them; all items of a class are independent.
 //
-// Per item (site, z, word) the single-spin sweep draws the item's four
-// Philox blocks (16 high uniform bits per replica), forms for each term of
-// the site the word of replicas whose term value is negative (the
-// two-spin-term table path: whose spin product is -1, its tables folding in
-// the weight's sign) and, for SQA, the two temporal disagreement words,
-// turns them into one threshold
-// index per replica (a per-site code table after an 8x8 bit-matrix
-// transpose, or byte-wise sums into the site's window of the threshold
-// row), and compares
-// the uniforms' high halves with the thresholds' through the carry of a
-// subtraction; only a tie of the high halves draws the low half
-// (probability 2^-16).  PT recounts energies for its swaps in bit-sliced
-// form.  The time-like cluster moves work one warp per (site, word) on the
-// site's whole imaginary-time ring.
+// Per item (site, z, word) the single-spin sweep draws the item's two
+// SWEEP_HI Philox blocks (one byte per replica, of which the uniform's 7-bit
+// high part), forms for each term of the site the word of replicas whose
+// term value is negative (the two-spin-term table path: whose spin product
+// is -1, its tables folding in the weight's sign) and, for SQA, the two
+// temporal disagreement words, turns them into one threshold byte per
+// replica (a per-site code table of the thresholds' top 7 bits after an 8x8
+// bit-matrix transpose, or byte-wise sums into the site's window of the
+// threshold row) and compares four replicas per instruction through the
+// borrow-free byte subtraction of a guard-bit word; a tie of the high parts
+// (probability 2^-7) goes to the block's tie array and is resolved after the
+// phase from the SWEEP_LO stream's low 25 bits.  PT recounts energies for
+// its swaps in bit-sliced form.  The time-like cluster moves work one warp
+// per (site, word) on the site's whole imaginary-time ring.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
