@@ -1237,9 +1237,10 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                 // each warp scans its share of the array, gathers the tied
                 // items on its list and resolves one tie of 32 of them at a
                 // time (every lane busy); items with ties left go back on
-                // the list.  The list holds 63 entries at most: fewer than
-                // 32 before a scan step adds at most 32, and a round takes
-                // 32 off before it puts at most 32 back.
+                // the list.  The list holds 63 entries at most: rounds run
+                // until fewer than 32 are left before a scan step adds at
+                // most 32 (a round takes 32 off before it puts at most 32
+                // back, and every round resolves 32 ties, so they end).
                 const uint32_t lt = (1u << lane) - 1u;
                 const auto round = [&](uint32_t nl) -> uint32_t {
                     __syncwarp();
@@ -1267,7 +1268,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
                     const uint32_t slot = nl + (uint32_t)__popc(bal & lt);
                     if (tmv && SQA_IN(kChkRequeue, slot, kRequeue)) rq[slot] = make_uint2(p, tmv);
                     nl += (uint32_t)__popc(bal);
-                    if (nl >= 32u) nl = round(nl);
+                    while (nl >= 32u) nl = round(nl);
                 }
                 while (nl > 0u) nl = round(nl);
             }
