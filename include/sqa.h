@@ -148,6 +148,16 @@ sqa_status sqa_get_info(const sqa_handle *h, sqa_info *out);
 sqa_status sqa_tune(sqa_handle *h, int32_t words_per_unit, int32_t use_table, int32_t cluster);
 sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t *use_table,
                           int32_t *smem_bytes, int32_t *cluster);
+/* Slices per thread of the single-spin sweep (another autotuner knob; results
+ * do not depend on it): each thread's task covers 1..4 consecutive slices
+ * (SQA: slices of one parity) or slots of one (site, word), so that the site's
+ * record and the word's hoisted random values are read once for several
+ * items.  0 (the default) lets the kernel choose per colour phase the count
+ * whose longest thread runs the fewest items.  slices outside 0..4 ->
+ * SQA_ERR_INVALID.  Takes effect at the next launch; the cluster moves ignore
+ * it. */
+sqa_status sqa_tune_slices(sqa_handle *h, int32_t slices);
+sqa_status sqa_get_task_slices(const sqa_handle *h, int32_t *slices);
 
 /* Runs the whole program: fresh initial spins, then sweeps 0..S-1 (SQA
  * anneal: Metropolis on the Trotterised H(t) of Eq. 3, App. B, Sec. III; or
@@ -264,8 +274,9 @@ sqa_status sqa_batch_create(sqa_handle *const *hs, int32_t n, sqa_batch **out);
 sqa_status sqa_batch_launch(sqa_batch *b, void *stream);
 /* Times the batch with 0 (the planner's words per unit for each job) and
  * 1, 2, 4, ... words per unit for every job (each job takes the largest of
- * W, ceil(W/2), ... not above it), n_trial sweeps each, and keeps the
- * fastest.  Synchronous; leaves the handles' spins at the end of a trial (a
+ * W, ceil(W/2), ... not above it), n_trial sweeps each, keeps the fastest,
+ * then with it times slices per task 0 (each job's own setting) and 1..4 for
+ * every job (see sqa_tune_slices) and keeps the fastest.  Synchronous; leaves the handles' spins at the end of a trial (a
  * launch starts from fresh initial spins).  words_per_unit and
  * attempts_per_s (either may be NULL) receive the choice and its trial
  * rate. */
@@ -276,7 +287,9 @@ sqa_status sqa_batch_autotune(sqa_batch *b, int32_t n_trial, void *stream, int32
 void sqa_batch_destroy(sqa_batch *b);
 /* Times h's sweep kernel in every launch shape that fits (cluster size 1, 2,
  * 4, 8, 16; table or window lookup; words per unit W, ceil(W/2), ..., 1) on
- * n_trial sweeps from sweep 0 and keeps the fastest (as sqa_tune).  h's
+ * n_trial sweeps from sweep 0 and keeps the fastest (as sqa_tune), then with
+ * that shape slices per task 0..4 (as sqa_tune_slices; not for cluster
+ * moves).  h's
  * spins are saved and restored.  Synchronous; the out pointers (may be
  * NULL) receive the choice and its trial rate in attempts/s. */
 sqa_status sqa_autotune(sqa_handle *h, int32_t n_trial, void *stream, int32_t *words_per_unit,

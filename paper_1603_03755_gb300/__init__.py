@@ -58,6 +58,8 @@ _SIGS = {
     "sqa_destroy": (None, [C.c_void_p]),
     "sqa_get_info": (C.c_int, [C.c_void_p, C.POINTER(_Info)]),
     "sqa_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "sqa_tune_slices": (C.c_int, [C.c_void_p, C.c_int32]),
+    "sqa_get_task_slices": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "sqa_get_launch": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_int32)]),
     "sqa_run": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -220,6 +222,10 @@ class Handle:
     def tune(self, words_per_unit: int = 0, use_table: int = -1, cluster: int = 0):
         _check(lib().sqa_tune(self._h, words_per_unit, use_table, cluster), "sqa_tune")
 
+    def tune_slices(self, slices: int = 0):
+        """Slices (or slots) per thread's task of the sweep, 1..4; 0 = automatic."""
+        _check(lib().sqa_tune_slices(self._h, int(slices)), "sqa_tune_slices")
+
     def autotune(self, n_trial: int = 20, stream=None) -> dict:
         """Times every launch shape that fits on n_trial sweeps and keeps the
         fastest (spins saved and restored); returns the choice."""
@@ -233,8 +239,10 @@ class Handle:
         wc, lut, smem, cl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib().sqa_get_launch(self._h, C.byref(wc), C.byref(lut), C.byref(smem), C.byref(cl)),
                "sqa_get_launch")
+        ts = C.c_int32()
+        _check(lib().sqa_get_task_slices(self._h, C.byref(ts)), "sqa_get_task_slices")
         return {"words_per_unit": wc.value, "use_table": lut.value, "smem_bytes": smem.value,
-                "cluster": cl.value}
+                "cluster": cl.value, "task_slices": ts.value}
 
     # ---- running ----
     def run(self, stream=None):

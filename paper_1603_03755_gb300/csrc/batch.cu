@@ -34,6 +34,7 @@ using namespace sqa;
 struct sqa_batch {
     std::vector<sqa_handle *> hs;
     int policy = 0;  // words per unit for every job (0: the planner's choice per job)
+    int slices = 0;  // slices per task for every job (0: each job's own setting)
     std::vector<JobDev> jobs;
     std::vector<Unit> units;
     std::vector<MultiGroup> groups;  // one persistent launch per path
@@ -73,6 +74,7 @@ sqa_status plan_batch(sqa_batch *b, int trial)
         if (st != SQA_OK) return st;
         J.t0 = 0;
         J.t1 = trial > 0 ? std::min(trial, h->S) : h->S;
+        if (b->slices > 0) J.task_slices = b->slices;
         b->jobs.push_back(J);
         for (Unit u : ju) {
             u.job = (int)k;
@@ -248,6 +250,27 @@ sqa_status sqa_batch_autotune(sqa_batch *b, int32_t n_trial, void *stream, int32
         }
     }
     b->policy = best < 0 ? keep : best;
+    // then slices per task, with that policy (0: each job's own setting)
+    const int keep_slices = b->slices;
+    int best_s = keep_slices;
+    if (best >= 0)
+        for (int sl = 0; sl <= kTaskSlices; sl++) {
+            b->slices = sl;
+            if (plan_batch(b, n_trial) != SQA_OK) continue;
+            double t = 0;
+            const sqa_status st = time_on(s, [&] { return launch_plain(b, s); }, &t);
+            if (st != SQA_OK) {
+                b->slices = keep_slices;
+                plan_batch(b, 0);
+                return st;
+            }
+            if (t < best_t) {
+                best_t = t;
+                best_s = sl;
+                best_rate = (double)batch_attempts(b) / t;
+            }
+        }
+    b->slices = best_s;
     const sqa_status st = plan_batch(b, 0);
     if (st != SQA_OK) return st;
     if (words_per_unit) *words_per_unit = b->policy;
@@ -284,7 +307,7 @@ sqa_status sqa_autotune(sqa_handle *h, int32_t n_trial, void *stream, int32_t *w
         cudaFreeAsync(saved, s);
         return cuda_fail(ecp, "sqa_autotune save");
     }
-    const int keep_wc = h->force_wc, keep_mode = h->force_mode, keep_c = h->force_cluster;
+    const int keep_wc = h->force_wc, keep_mode = h->force_mode, keep_c = h->force_cluster, keep_s = h->force_slices;
     const int64_t attempts = (int64_t)h->job.n * h->job.Z * h->R * h->I * trial;
     struct Choice {
         int wc, lut, C;
@@ -306,7 +329,20 @@ sqa_status sqa_autotune(sqa_handle *h, int32_t n_trial, void *stream, int32_t *w
             }
             if (st != SQA_OK) break;
         }
-    const sqa_status rs = best.t > 0 ? sqa_tune(h, best.wc, best.lut, best.C) : sqa_tune(h, keep_wc, keep_mode, keep_c);
+    sqa_status rs = best.t > 0 ? sqa_tune(h, best.wc, best.lut, best.C) : sqa_tune(h, keep_wc, keep_mode, keep_c);
+    // then slices per task with the chosen shape (0: the kernel's own choice)
+    int best_s = keep_s;
+    if (rs == SQA_OK && st == SQA_OK && best.t > 0 && h->move != SQA_MOVE_WOLFF)
+        for (int sl = 0; sl <= kTaskSlices && st == SQA_OK; sl++) {
+            sqa_tune_slices(h, sl);
+            double t = 0;
+            st = time_on(s, [&] { return run_sweeps(h, 0, trial, s); }, &t);
+            if (st == SQA_OK && t < best.t) {
+                best.t = t;
+                best_s = sl;
+            }
+        }
+    if (rs == SQA_OK) sqa_tune_slices(h, best_s);
     cudaMemcpyAsync(h->d_state, saved, bytes, cudaMemcpyDeviceToDevice, s);
     cudaFreeAsync(saved, s);
     const cudaError_t e = cudaStreamSynchronize(s);

@@ -446,6 +446,7 @@ sqa_status setup_program(sqa_handle *h)
     J.swap_every = h->swap_every;
     J.csize = 1;
     J.zr = J.Z;
+    J.task_slices = h->force_slices;
     J.t0 = 0;
     J.t1 = h->S;
     J.seed_lo = (uint32_t)h->seed;
@@ -1012,6 +1013,23 @@ sqa_status sqa_get_launch(const sqa_handle *h, int32_t *words_per_unit, int32_t 
     if (use_table) *use_table = h->job.use_lut;
     if (smem_bytes) *smem_bytes = h->job.smem_bytes;
     if (cluster) *cluster = h->job.csize;
+    return SQA_OK;
+}
+
+sqa_status sqa_tune_slices(sqa_handle *h, int32_t slices)
+{
+    const sqa_status us = usable(h);
+    if (us != SQA_OK) return us;
+    if (slices < 0 || slices > kTaskSlices) return set_error("slices per task: 0..4"), SQA_ERR_INVALID;
+    h->force_slices = slices;
+    h->job.task_slices = slices;
+    return SQA_OK;
+}
+
+sqa_status sqa_get_task_slices(const sqa_handle *h, int32_t *slices)
+{
+    if (!h || !slices) return set_error("NULL argument"), SQA_ERR_INVALID;
+    *slices = h->job.task_slices;
     return SQA_OK;
 }
 

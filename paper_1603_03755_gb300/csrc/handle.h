@@ -31,6 +31,7 @@ struct sqa_handle {
     int smax = 0, dmin = 0, dmax = 0, nd = 0;
     bool window_limit_exceeded = false;
     int force_wc = 0, force_mode = -1, force_cluster = 0;  // sqa_tune overrides (0 / -1: automatic)
+    int force_slices = 0;  // sqa_tune_slices override (0: automatic)
     // device
     sqa::JobDev job{};
     uint32_t *d_state = nullptr;

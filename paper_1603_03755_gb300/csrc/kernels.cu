@@ -1151,7 +1151,9 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
     int cz[kMaxColours];
 #pragma unroll
     for (int c = 0; c < kMaxColours; c++)
-        cz[c] = c < J.ncol ? chunk_for((J.col_ptr[c + 1] - J.col_ptr[c]) * wc, zn, nthr) : 1;
+        cz[c] = c >= J.ncol ? 1
+                : J.task_slices > 0 ? min(min(J.task_slices, kTaskSlices), zn)
+                                    : chunk_for((J.col_ptr[c + 1] - J.col_ptr[c]) * wc, zn, nthr);
     const int warp = tid >> 5, lane = tid & 31;
     uint2 *rq = sm.rq + (size_t)warp * kRequeue;
 

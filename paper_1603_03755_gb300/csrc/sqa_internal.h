@@ -99,6 +99,7 @@ struct JobDev {
     int csize;       // blocks per unit (a thread-block cluster when > 1)
     int zr;          // slices (SQA) or slots (PT) per block: Z / csize
     int pairs;       // every term has two spins (minor embedding)
+    int task_slices; // single-spin sweep: slices (SQA: slice pairs) or slots per task, 1..4; 0 = the kernel's choice
     // time-like cluster moves (SQA, move == SQA_MOVE_WOLFF)
     int move;
     uint32_t key_wstart, key_wbond, key_wacc;  // seed_hi ^ kDomW*

@@ -258,3 +258,11 @@ def test_checked_build_compiles_and_exports_every_symbol():
             "assert not missing, missing; assert L.sqa_bounds_checked() == 1; print('ok')")
     r = subprocess.run([sys.executable, "-c", code, path, *names], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr
+
+
+def test_slices_knob_validates_before_device_work(L):
+    """sqa_tune_slices / sqa_get_task_slices answer a NULL handle with
+    SQA_ERR_INVALID, before any device call."""
+    v = C.c_int32()
+    assert L.sqa_tune_slices(None, 2) == pkg.SQA_ERR_INVALID
+    assert L.sqa_get_task_slices(None, C.byref(v)) == pkg.SQA_ERR_INVALID

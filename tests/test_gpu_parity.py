@@ -325,6 +325,42 @@ def test_launch_shapes_give_the_oracle_bits(emb, use_table, wc):
         assert np.array_equal(st[i], q.s)
 
 
+@pytest.mark.parametrize("kind,emb,slices", [("sqa", "me", 1), ("sqa", "me", 3), ("sqa", "lhz", 4),
+                                            ("sqa", "lhz", 2), ("pt", "me", 3), ("pt", "lhz", 1)])
+def test_slices_per_task_give_the_oracle_bits(kind, emb, slices):
+    """Forced slices (or slots) per thread's task, 1..4, including counts that
+    do not divide the slice pairs (L = 14: 7 per parity) or the slots (P = 7):
+    same bits."""
+    N, R, S = 7, 70, 15
+    pen = 6 if emb == "me" else 9
+    J = W.random_instances(N, 2, 600 + slices)
+    kw = dict(embedding=emb, N=N, J=J, penalty=pen, sweeps=S, R=R, seed=600 + slices, kind=kind)
+    if kind == "sqa":
+        kw.update(L=14, beta=3.0)
+    else:
+        kw.update(betas=W.geometric_ladder(7, 5.0, 0.2), swap_every=1)
+    h = pkg.Handle(**kw)
+    h.tune_slices(slices)
+    assert h.launch()["task_slices"] == slices
+    h.run(stream=0)
+    st = gpu_state(h)
+    E = h.energies(stream=0)
+    for i in range(2):
+        pb = O.Problem(emb, N, J[i], pen)
+        if kind == "sqa":
+            A, B = O.linear_schedule(S)
+            q = O.SQA(pb, 14, R, 3.0, A, B, 600 + slices, i)
+            q.run(0, S)
+            assert np.array_equal(st[i], q.s)
+        else:
+            o = O.PT(pb, kw["betas"], R, 1, 600 + slices, i)
+            o.run(0, S)
+            assert np.array_equal(st[i], o.s) and np.array_equal(E[i], o.E)
+    with pytest.raises(pkg.SQAError):
+        h.tune_slices(5)
+    h.close()
+
+
 def test_oversized_unit_is_refused():
     """One 32-replica word of LHZ K_64 at L = 1024 is 8 MB of state, more than
     a 16-block cluster's shared memory: the job is refused at planning (no
