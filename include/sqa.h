@@ -276,7 +276,9 @@ sqa_status sqa_batch_launch(sqa_batch *b, void *stream);
  * 1, 2, 4, ... words per unit for every job (each job takes the largest of
  * W, ceil(W/2), ... not above it), n_trial sweeps each, keeps the fastest,
  * then with it times slices per task 0 (each job's own setting) and 1..4 for
- * every job (see sqa_tune_slices) and keeps the fastest.  Synchronous; leaves the handles' spins at the end of a trial (a
+ * every job (see sqa_tune_slices), then the SQA threshold lookup of every
+ * job (its own plan, code tables, byte windows; a job that a form does not
+ * fit keeps its own), keeping the fastest at each step.  Synchronous; leaves the handles' spins at the end of a trial (a
  * launch starts from fresh initial spins).  words_per_unit and
  * attempts_per_s (either may be NULL) receive the choice and its trial
  * rate. */

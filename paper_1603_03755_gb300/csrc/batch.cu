@@ -35,6 +35,7 @@ struct sqa_batch {
     std::vector<sqa_handle *> hs;
     int policy = 0;  // words per unit for every job (0: the planner's choice per job)
     int slices = 0;  // slices per task for every job (0: each job's own setting)
+    int lookup = -1; // SQA threshold lookup for every job: 1 tables, 0 windows, -1 each job's own plan
     std::vector<JobDev> jobs;
     std::vector<Unit> units;
     std::vector<MultiGroup> groups;  // one persistent launch per path
@@ -70,7 +71,15 @@ sqa_status plan_batch(sqa_batch *b, int trial)
             f = h->job.W;
             while (f > b->policy && f > 1) f = (f + 1) / 2;
         }
-        const sqa_status st = plan_job(h, 1, f, J, ju);
+        const int keep_mode = h->force_mode;
+        if (b->lookup >= 0 && h->kind == SQA_KIND_SQA && !(b->lookup == 0 && h->window_limit_exceeded))
+            h->force_mode = b->lookup;
+        sqa_status st = plan_job(h, 1, f, J, ju);
+        if (st != SQA_OK && h->force_mode != keep_mode) {  // that lookup does not fit this job: its own plan
+            h->force_mode = keep_mode;
+            st = plan_job(h, 1, f, J, ju);
+        }
+        h->force_mode = keep_mode;
         if (st != SQA_OK) return st;
         J.t0 = 0;
         J.t1 = trial > 0 ? std::min(trial, h->S) : h->S;
@@ -271,6 +280,28 @@ sqa_status sqa_batch_autotune(sqa_batch *b, int32_t n_trial, void *stream, int32
             }
         }
     b->slices = best_s;
+    // then the SQA threshold lookup for every job (tables or windows; -1 each
+    // job's own plan), with those settings
+    const int keep_lookup = b->lookup;
+    int best_l = keep_lookup;
+    if (best >= 0)
+        for (int lk : {-1, 1, 0}) {
+            b->lookup = lk;
+            if (plan_batch(b, n_trial) != SQA_OK) continue;
+            double t = 0;
+            const sqa_status st = time_on(s, [&] { return launch_plain(b, s); }, &t);
+            if (st != SQA_OK) {
+                b->lookup = keep_lookup;
+                plan_batch(b, 0);
+                return st;
+            }
+            if (t < best_t) {
+                best_t = t;
+                best_l = lk;
+                best_rate = (double)batch_attempts(b) / t;
+            }
+        }
+    b->lookup = best_l;
     const sqa_status st = plan_batch(b, 0);
     if (st != SQA_OK) return st;
     if (words_per_unit) *words_per_unit = b->policy;
