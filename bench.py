@@ -31,6 +31,11 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The serving loop keeps many streams' work in flight (chunks, packs, uploads,
+# result copies); with the default 8 hardware work queues unrelated streams
+# share queues and wait on each other.  Set before CUDA starts (a serving
+# deployment sets it the same way); no other part of the bench depends on it.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import workloads as W  # noqa: E402
 

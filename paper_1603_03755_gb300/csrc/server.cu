@@ -56,9 +56,12 @@ constexpr int kOwnStreams = 32;  // pool streams 0..31: jobs with their own laun
 constexpr int kPackSplit = 2;    // packs a set of ready jobs is cut into (their tails overlap)
 constexpr int kAdmitBatch = 16;  // jobs admitted per pass of the worker
 // Ready jobs are packed only when the resident jobs hold at least this many
-// units per SM (about two waves of the sweep kernels' blocks); below it each
-// runs its own chunk launch.
-constexpr int kPackMinUnitsPerSM = 6;
+// units per SM (more than a wave of the sweep kernels' blocks); below it each
+// runs its own chunk launch.  On the serving benchmark's stream (with 32
+// hardware connections): packing always gave the highest saturated capacity
+// (3.79e11 attempts/s) but p99 latencies of 6.2-8.2 s under Poisson load;
+// 4 gave 3.03e11 and 4.6-5.3 s, 2 gave 2.88e11 and 4.6-5.2 s.
+constexpr int kPackMinUnitsPerSM = 4;
 // Default attempts per unit per chunk: on the serving benchmark's job stream
 // (200 jobs, all at once) 1e7 finished in 14.9 s, against 15.4 s (5e6),
 // 18.3 s (2e6), 18.3 s (4e7 with 16-block clusters for long jobs) and 16.3 s
