@@ -95,7 +95,6 @@ struct Smem {
     SiteRec *sites;   // [n]
     int32_t *E;       // PT: [zr][wc*32]
     uint32_t *M;      // PT: swap masks [zr/2+1][wc]
-    uint32_t *qn;     // tie queue counters (two, used by alternate phases)
     uint32_t *qdiv;   // per colour: the task decode's divisor {m, sh} (FastDiv)
     uint32_t *tq;     // this block's tie array: one tie mask per item of a phase (global memory)
     uint32_t tq_words;  // its length in words
@@ -117,7 +116,6 @@ __device__ __forceinline__ Smem carve(const JobDev &J, unsigned char *base)
     m.sites = (SiteRec *)(base + o.sites);
     m.E = (int32_t *)(base + o.E);
     m.M = (uint32_t *)(base + o.M);
-    m.qn = (uint32_t *)(base + o.Q);
     m.qdiv = (uint32_t *)(base + o.Q + 16);
     m.tq = (uint32_t *)(J.tieq + (size_t)blockIdx.x * (size_t)J.tieq_stride);
     m.tq_words = 2u * (uint32_t)J.tieq_stride;
@@ -1139,7 +1137,6 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
         sm.rec[2 * si] = make_uint4(rec[0], rec[1], rec[2], rec[3]);
         sm.rec[2 * si + 1] = make_uint4(rec[4], rec[5], rec[6], rec[7]);
     }
-    if (tid < 2) sm.qn[tid] = 0u;
     if (tid < J.ncol) {
         const FastDiv f = make_div((uint32_t)(J.col_ptr[tid + 1] - J.col_ptr[tid]));
         sm.qdiv[2 * tid] = f.m;
@@ -1157,7 +1154,6 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
     const int warp = tid >> 5, lane = tid & 31;
     uint2 *rq = sm.rq + (size_t)warp * kRequeue;
 
-    int ph = 0;  // running phase index: the tie queue counters alternate
     for (int t = J.t0; t < J.t1; t++) {
         const PhiloxSweep ps = philox_sweep(J, (uint32_t)t, (uint32_t)inst);
         if (tid < 2 * wc) sm.ph[tid] = philox_word(J, ps, (uint32_t)(w0 + (tid >> 1)), (uint32_t)(tid & 1));
@@ -1175,7 +1171,7 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
         }
         if (KIND == SQA_KIND_PT) __syncthreads();  // the sweep's hoisted Philox values
         const int nph = KIND == SQA_KIND_SQA ? 2 * J.ncol : J.ncol;
-        for (int cls = 0; cls < nph; cls++, ph++) {
+        for (int cls = 0; cls < nph; cls++) {
             const int chi = KIND == SQA_KIND_SQA ? cls >> 1 : cls, par = KIND == SQA_KIND_SQA ? cls & 1 : 0;
             const int c0 = J.col_ptr[chi], nq = J.col_ptr[chi + 1] - c0;
             int czc = cz[0];

@@ -27,7 +27,7 @@ struct SmemOffsets {
     size_t sites;  // SiteRec [n]
     size_t E;      // PT: energies [P][wc*32]
     size_t M;      // PT: swap masks [P/2+1][wc]; cluster moves: per-warp start masks [8][64 or 128]
-    size_t Q;      // 64 bytes: two tie-queue counters, and per colour the divisor of the task decode
+    size_t Q;      // 64 bytes: from byte 16, per colour the divisor of the task decode
     size_t P;      // single-spin sweep: per word of the unit and SWEEP_HI block, the sweep's
                    // slice-independent Philox values {P0, Q2, O3, 0} (4 words)
     size_t R;      // single-spin sweep: per site, the tie record (kTieRec bytes)
