@@ -604,6 +604,31 @@ int grid_for(const void *kernel, int smem_bytes, int n_units, int threads)
     return std::max(1, std::min(n_units, per_sm * g_num_sms));
 }
 
+// Threads per block of a path's multi-job launch: the path's own width,
+// except that SQA single-spin units so small that a 256-thread block would
+// hold under kSmallItems items per thread per colour phase (weighted by the
+// units' work) run 128-thread blocks, twice as many per SM; the kernels size
+// themselves from blockDim.  Measured (2000 sweeps, one session): 256
+// one-instance ME K_12 jobs 9.02e11 -> 1.10e12 attempts/s; the ragged LHZ/ME
+// mix, whose units mostly stay at 256, 8.91e11 -> 8.84e11; forcing 128 on
+// every group took the mix to 7.68e11.
+constexpr double kSmallItems = 4.0;
+
+static int multi_threads(const std::vector<JobDev> &jobs, const std::vector<Unit> &units, int mode, size_t i, size_t j)
+{
+    const int full = sweep_mode_threads(mode);
+    if (mode != 1 && mode != 2 && mode != 5) return full;
+    double items = 0, work = 0;
+    for (size_t u = i; u < j; u++) {
+        const JobDev &x = jobs[units[u].job];
+        if (2 * units[u].wc > 128) return full;  // a block stages the hoisted values of 2 x wc words
+        const double w = (double)x.n * x.zr * units[u].wc;  // items per sweep
+        items += w / (2.0 * x.ncol * full) * w;            // per thread and phase, weighted by work
+        work += w;
+    }
+    return work > 0 && items / work < kSmallItems ? 128 : full;
+}
+
 int group_units(const std::vector<JobDev> &jobs, std::vector<Unit> &units, std::vector<MultiGroup> &groups)
 {
     // by path, then longest units first so the tail of each launch is short
@@ -626,7 +651,8 @@ int group_units(const std::vector<JobDev> &jobs, std::vector<Unit> &units, std::
         g.u0 = (int)i;
         g.n = (int)(j - i);
         g.smem = smem;
-        g.grid = grid_for(sweep_multi_entry(mode), smem, g.n, sweep_mode_threads(mode));
+        g.threads = multi_threads(jobs, units, mode, i, j);
+        g.grid = grid_for(sweep_multi_entry(mode), smem, g.n, g.threads);
         g.row0 = 0;
         groups.push_back(g);
         i = j;
@@ -691,6 +717,18 @@ void assign_tieq(std::vector<JobDev> &jobs, const std::vector<MultiGroup> &group
     }
 }
 
+// One group's persistent launch, at its block width.
+static cudaError_t launch_group(const MultiGroup &g, const JobDev *d_jobs, const Unit *d_units, int *d_counters,
+                                cudaStream_t s)
+{
+    const Unit *units = d_units + g.u0;
+    int n = g.n;
+    int *counter = d_counters + g.mode;
+    void *args[] = {(void *)&d_jobs, (void *)&units, (void *)&n, (void *)&counter};
+    return cudaLaunchKernel(sweep_multi_entry(g.mode), dim3((unsigned)g.grid), dim3((unsigned)g.threads), args,
+                            (size_t)g.smem, s);
+}
+
 cudaError_t launch_groups(const std::vector<MultiGroup> &groups, const JobDev *d_jobs, const Unit *d_units,
                           int *d_counters, cudaStream_t s, bool fork)
 {
@@ -699,7 +737,7 @@ cudaError_t launch_groups(const std::vector<MultiGroup> &groups, const JobDev *d
     if (groups.size() == 1 || !fork) {
         for (size_t k = 0; k < groups.size() && e == cudaSuccess; k++) {
             const MultiGroup &g = groups[k];
-            e = launch_sweep_multi(g.mode, g.grid, g.smem, d_jobs, d_units + g.u0, g.n, d_counters + g.mode, s);
+            e = launch_group(g, d_jobs, d_units, d_counters, s);
         }
         return e;
     }
@@ -714,7 +752,7 @@ cudaError_t launch_groups(const std::vector<MultiGroup> &groups, const JobDev *d
         const MultiGroup &g = groups[k];
         e = cudaStreamWaitEvent(p->st[k], p->fork, 0);
         if (e == cudaSuccess)
-            e = launch_sweep_multi(g.mode, g.grid, g.smem, d_jobs, d_units + g.u0, g.n, d_counters + g.mode, p->st[k]);
+            e = launch_group(g, d_jobs, d_units, d_counters, p->st[k]);
         if (e == cudaSuccess) e = cudaEventRecord(p->join[k], p->st[k]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->join[k], 0);
     }

@@ -106,7 +106,7 @@ cudaError_t launch_sweep_multi(int mode, int grid, int smem, const JobDev *jobs,
 // The launches run concurrently, so each has its own rows of the tie queue
 // (JobDev::tieq), from row row0.
 struct MultiGroup {
-    int mode, u0, n, smem, grid, row0;
+    int mode, u0, n, smem, grid, row0, threads;
 };
 // Sorts units by path (longest first within a path) into groups, sizes their
 // launches and orders them by work; returns the tie-queue rows of all groups.
