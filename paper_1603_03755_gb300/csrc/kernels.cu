@@ -1297,8 +1297,8 @@ __device__ void run_unit(const JobDev &J, const Smem &sm, const Unit &u)
 // cost the same).  The two-spin-term table path (5) folds the weights' signs
 // into its code tables (FOLD): the items never load the weights.  Measured
 // against term-value codes: +4.7 % on this path, while folding on the
-// general-term path and in the multi-job kernel ran 0.6 % and 2.8 % slower,
-// so they keep term-value codes.
+// general-term path ran 0.6 % slower, so that path keeps term-value codes.
+// The multi-job kernels below are instantiated per path the same way.
 template <int MODE>
 __global__ void __launch_bounds__(MODE == 0 || MODE == 6 ? 384 : 256, MODE == 3 ? 4 : (MODE == 0 || MODE == 6 ? 2 : 3))
     sweep_kernel_one(const __grid_constant__ JobDev J, const Unit *units, int n_units, int *counter)
